@@ -1,0 +1,155 @@
+/*
+ * eapdtw.h - C ABI of the GB300 (sm_103a) EAPrunedDTW subsequence-search library.
+ *
+ * Method: Herrmann & Webb, "Early Abandoning PrunedDTW and its application to
+ * similarity search" (arXiv 2010.05371).  DTW is the recurrence of Eq. 1-5 with
+ * the squared Euclidean cost (Section 2); the warping window w is the
+ * Sakoe-Chiba band |i - j| <= w (Section 2.1); early abandoning against an
+ * upper bound ub follows Algorithm 3 (EAPrunedDTW) and Section 2.2; the search
+ * is the UCR-Suite loop of Section 5 (z-normalised sliding windows, LB_Kim and
+ * LB_Keogh lower bounds, best-so-far tightening).
+ *
+ * Conventions shared by every entry point:
+ *  - Return value: EAPDTW_OK (0) or a negative EAPDTW_ERR_* code.  No C++
+ *    exception crosses this boundary.  eapdtw_strerror() names a code.
+ *  - Unless a name ends in _host, array arguments are DEVICE pointers (memory
+ *    of the current CUDA device, e.g. allocated by PyTorch), owned by the
+ *    caller; the library never frees them and keeps no reference after the
+ *    call returns.  _host variants take host pointers and copy.
+ *  - Series are float32, contiguous.  Distances are returned as float64
+ *    holding the float32 DTW value (a sum of squared costs, no square root).
+ *  - stream: a cudaStream_t (NULL = the legacy default stream).  Every call
+ *    enqueues its work on that stream; calls documented as "blocking"
+ *    additionally wait for it before returning.
+ *  - Scratch memory (prefix sums, envelopes, queues) is owned by the library,
+ *    cached per device and grown on demand; it is released by
+ *    eapdtw_release_scratch() or at process exit.  Calls on one device from
+ *    several host threads are serialised internally.
+ *  - Window semantics: cell (i, j) exists iff |i - j| <= w.  w >= max(lS,lT)-1
+ *    is unconstrained DTW.  w < |lS - lT| admits no warping path: the result
+ *    is +inf.
+ */
+#ifndef EAPDTW_H
+#define EAPDTW_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define EAPDTW_OK 0
+#define EAPDTW_ERR_INVALID_ARG -1   /* NULL pointer, length <= 0, w < 0, k < 1, NaN ub, lQ > lR */
+#define EAPDTW_ERR_NAN_INPUT -2     /* a NaN or Inf in an input series */
+#define EAPDTW_ERR_OUT_OF_MEMORY -3 /* scratch allocation failed */
+#define EAPDTW_ERR_CUDA -4          /* a CUDA runtime call failed */
+#define EAPDTW_ERR_TIMEOUT -5       /* a device-side wait exceeded its budget */
+#define EAPDTW_ERR_UNSUPPORTED -6   /* size beyond what this build supports (see each call) */
+#define EAPDTW_ERR_INTERNAL -7      /* a device-side consistency check failed */
+
+/* Upper limits of this build.  The query (shorter series) length is bounded
+ * by the query staging buffer in shared memory. */
+#define EAPDTW_MAX_QUERY 8192
+#define EAPDTW_MAX_K 64
+
+/* Counters of one search (indices into the int64 counter array). */
+#define EAPDTW_CNT_WINDOWS 0        /* candidate windows scanned */
+#define EAPDTW_CNT_KIM_PRUNED 1     /* skipped by LB_Kim > ub */
+#define EAPDTW_CNT_EQ_PRUNED 2      /* skipped by LB_Keogh(EQ) > ub */
+#define EAPDTW_CNT_EC_PRUNED 3      /* skipped by LB_Keogh(EC) > ub */
+#define EAPDTW_CNT_DTW_ABANDONED 4  /* EAPrunedDTW returned +inf (DTW > ub) */
+#define EAPDTW_CNT_DTW_COMPLETED 5  /* EAPrunedDTW returned a value <= ub */
+#define EAPDTW_CNT_CELLS 6          /* DP cells executed by the kernel (K per busy lane-step) */
+#define EAPDTW_CNT_LB_RECHECK 7     /* LB re-tested against a tighter ub before DTW and skipped */
+#define EAPDTW_CNT_OVERFLOW 8       /* candidates re-run with a wider tile */
+#define EAPDTW_CNT_STEPS 9          /* warp wavefront steps executed */
+#define EAPDTW_NCOUNTERS 16
+
+/* eapdtw_strerror: static description of a return code (never NULL). */
+const char* eapdtw_strerror(int32_t code);
+
+/* eapdtw_version: library version string (static). */
+const char* eapdtw_version(void);
+
+/*
+ * eap_dtw - DTW of two raw series with early abandoning (Algorithm 3).
+ *
+ * Computes DTW_w(S, T) per Eq. 1-5 (cost (a - b)^2, band |i - j| <= w) on the
+ * raw values (no z-normalisation).  *out_dist receives the DTW value if it is
+ * <= ub, else +inf (Algorithm 3 returns +inf exactly when DTW > ub).
+ * ub = +INFINITY gives plain banded DTW.
+ *
+ *   S, T      device float32 arrays of lS and lT points (lS, lT >= 1).
+ *   w         window, w >= 0.
+ *   ub        upper bound; not NaN.
+ *   out_dist  DEVICE pointer to one double.
+ *   stream    cudaStream_t.  Asynchronous: the result is valid once the stream
+ *             reaches this point.
+ * Errors: INVALID_ARG; UNSUPPORTED if min(lS, lT) > EAPDTW_MAX_PAIR_COLS.
+ */
+#define EAPDTW_MAX_PAIR_COLS 65536
+int32_t eap_dtw(const float* S, int64_t lS, const float* T, int64_t lT, int64_t w, double ub,
+                double* out_dist, void* stream);
+
+/* eap_dtw_host - eap_dtw on host arrays; blocking; *out_dist is a host double. */
+int32_t eap_dtw_host(const float* S, int64_t lS, const float* T, int64_t lT, int64_t w,
+                     double ub, double* out_dist);
+
+/*
+ * subseq_search - k nearest subsequences of R to Q under DTW (Section 5).
+ *
+ * Every window R[i .. i+lQ), i in [0, lR - lQ], and the query Q are
+ * z-normalised (population standard deviation; a constant window normalises to
+ * zeros); d_i = DTW_w(z(window_i), z(Q)) with the window as rows and the query
+ * as columns.  Returns the k smallest (d_i, i), ascending by (d_i, i); a
+ * distance tie goes to the smaller i.  Windows may overlap (no exclusion zone).
+ * If k > lR - lQ + 1 the extra slots are (-1, +inf).
+ *
+ * The search runs LB_Kim (first/last points), LB_Keogh EQ (window against the
+ * query envelope) and LB_Keogh EC (query against the reference envelope), then
+ * EAPrunedDTW against the running k-th best distance; these never change the
+ * result, only the work done.
+ *
+ *   Q         device float32 [lQ], 1 <= lQ <= EAPDTW_MAX_QUERY.
+ *   R         device float32 [lR], lR >= lQ, lR < 2^31.
+ *   w         window, w >= 0 (w >= lQ - 1 is unconstrained).
+ *   k         1 <= k <= EAPDTW_MAX_K.
+ *   out_idx   DEVICE int64 [k];  out_dist  DEVICE double [k].
+ *   stream    cudaStream_t.  Blocking: returns after the results are written.
+ * Errors: INVALID_ARG, NAN_INPUT (NaN/Inf in Q or R), UNSUPPORTED, OUT_OF_MEMORY,
+ *         CUDA.
+ */
+int32_t subseq_search(const float* Q, int64_t lQ, const float* R, int64_t lR, int64_t w,
+                      int32_t k, int64_t* out_idx, double* out_dist, void* stream);
+
+/* Options of subseq_search_ex (zero-initialise, then set fields). */
+typedef struct {
+    int32_t no_lb;        /* 1: skip LB_Kim / LB_Keogh ("nolb" variant of Section 5) */
+    int32_t tile;         /* DP cells per lane per step (4, 8, 16, 32); 0 = automatic */
+    int32_t no_seed;      /* 1: start from ub = +inf instead of a sampled seed */
+    int32_t audit;        /* 1: hold ub fixed at ub_fixed for the whole search */
+    double ub_fixed;      /* used when audit = 1 */
+    int64_t* counters;    /* optional HOST int64[EAPDTW_NCOUNTERS], filled on return */
+    int32_t reserved[8];
+} eapdtw_search_opts;
+
+/* subseq_search_ex - subseq_search with options (opts may be NULL). */
+int32_t subseq_search_ex(const float* Q, int64_t lQ, const float* R, int64_t lR, int64_t w,
+                         int32_t k, const eapdtw_search_opts* opts, int64_t* out_idx,
+                         double* out_dist, void* stream);
+
+/* subseq_search_host - subseq_search on HOST arrays (Q, R, out_idx, out_dist),
+ * copying inputs to the device and results back; blocking. */
+int32_t subseq_search_host(const float* Q, int64_t lQ, const float* R, int64_t lR, int64_t w,
+                           int32_t k, const eapdtw_search_opts* opts, int64_t* out_idx,
+                           double* out_dist);
+
+/* eapdtw_release_scratch - free the cached scratch memory of the current device. */
+int32_t eapdtw_release_scratch(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* EAPDTW_H */
