@@ -426,8 +426,8 @@ int orc_search_brute(const double* Q, int64_t m, const double* R, int64_t n, int
 /*                                                                          */
 /*  - EQ: the candidate against the query's envelope over +-w, clipped to    */
 /*    the query.  EC: the query against the envelope of the raw reference    */
-/*    over +-w (not clipped to the window), normalised with the window's     */
-/*    mean and deviation; a constant window normalises it to zeros.          */
+/*    over +-min(w, m-1) (not clipped to the window), normalised with the    */
+/*    window's mean and deviation; a constant window normalises to zeros.    */
 /*  - use_lb = 0 skips all three bounds ("nolb", Section 5).                 */
 /*  - ub_fixed: NaN for the running k-th best; a number fixes ub for the     */
 /*    whole scan (audit mode: pruning counts no longer depend on order).     */
@@ -513,9 +513,13 @@ int orc_search_cascade(const double* Q, int64_t m, const double* R, int64_t n, i
     orc_znorm(Q, m, zq);
     orc_envelope(zq, m, w, uq, lq);
     if (use_lb) {
+        /* READING: the EC envelope radius is min(w, m - 1).  A window point is
+         * only ever aligned with points of the same window, which lie within
+         * m - 1 of it; any radius >= that gives a valid (superset) envelope,
+         * and m - 1 is the tightest such radius for w >= m - 1. */
         ur = (double*)malloc(sizeof(double) * (size_t)n);
         lr = (double*)malloc(sizeof(double) * (size_t)n);
-        orc_envelope(R, n, w, ur, lr);
+        orc_envelope(R, n, w < m - 1 ? w : m - 1, ur, lr);
     }
     topk_t t = {k, 0, (double*)malloc(sizeof(double) * (size_t)k),
                 (int64_t*)malloc(sizeof(int64_t) * (size_t)k)};
