@@ -50,7 +50,7 @@ extern "C" {
 
 /* Upper limits of this build.  The query (shorter series) length is bounded
  * by the query staging buffer in shared memory. */
-#define EAPDTW_MAX_QUERY 8192
+#define EAPDTW_MAX_QUERY 4096
 #define EAPDTW_MAX_K 64
 
 /* Counters of one search (indices into the int64 counter array). */

@@ -1,0 +1,199 @@
+"""Python binding of libeapdtw.so (argument marshalling only).
+
+Every function here forwards to the C ABI declared in include/eapdtw.h; all
+computation runs in the library's CUDA kernels.  Device-array functions take
+CUDA float32 tensors; the *_host functions take numpy arrays.  If the library
+is not built, the first call raises: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+import os
+import re
+
+import numpy as np
+
+from . import build as _build
+
+_lib = None
+
+_HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include",
+                       "eapdtw.h")
+
+NCOUNTERS = 16
+COUNTER_NAMES = ("windows", "kim_pruned", "eq_pruned", "ec_pruned", "dtw_abandoned",
+                 "dtw_completed", "cells", "lb_recheck", "overflow", "steps")
+
+
+class SearchOpts(C.Structure):
+    _fields_ = [
+        ("no_lb", C.c_int32),
+        ("tile", C.c_int32),
+        ("no_seed", C.c_int32),
+        ("audit", C.c_int32),
+        ("ub_fixed", C.c_double),
+        ("counters", C.POINTER(C.c_int64)),
+        ("reserved", C.c_int32 * 8),
+    ]
+
+
+class EapDtwError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        super().__init__(f"{what}: {strerror(code)} ({code})")
+        self.code = code
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib():
+    """Load libeapdtw.so (it must have been built by build.build())."""
+    global _lib
+    if _lib is None:
+        path = _build.LIB
+        if not os.path.exists(path):
+            raise RuntimeError(f"{path} is missing: build it with paper_2010_05371_gb300.build.build()")
+        L = C.CDLL(path)
+        vp, i64, i32, dbl = C.c_void_p, C.c_int64, C.c_int32, C.c_double
+        L.eapdtw_strerror.restype = C.c_char_p
+        L.eapdtw_strerror.argtypes = [i32]
+        L.eapdtw_version.restype = C.c_char_p
+        L.eapdtw_version.argtypes = []
+        L.eap_dtw.restype = i32
+        L.eap_dtw.argtypes = [vp, i64, vp, i64, i64, dbl, vp, vp]
+        L.eap_dtw_host.restype = i32
+        L.eap_dtw_host.argtypes = [vp, i64, vp, i64, i64, dbl, C.POINTER(dbl)]
+        L.subseq_search.restype = i32
+        L.subseq_search.argtypes = [vp, i64, vp, i64, i64, i32, vp, vp, vp]
+        L.subseq_search_ex.restype = i32
+        L.subseq_search_ex.argtypes = [vp, i64, vp, i64, i64, i32, C.POINTER(SearchOpts), vp, vp, vp]
+        L.subseq_search_host.restype = i32
+        L.subseq_search_host.argtypes = [vp, i64, vp, i64, i64, i32, C.POINTER(SearchOpts), vp, vp]
+        L.eapdtw_release_scratch.restype = i32
+        L.eapdtw_release_scratch.argtypes = []
+        _lib = L
+    return _lib
+
+
+def header_functions(path: str = _HEADER):
+    """Names of the functions declared in include/eapdtw.h."""
+    with open(path) as f:
+        text = f.read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return re.findall(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\*?\s*([A-Za-z_][A-Za-z0-9_]*)\s*\(",
+                      text, flags=re.M)
+
+
+def strerror(code: int) -> str:
+    return lib().eapdtw_strerror(int(code)).decode()
+
+
+def version() -> str:
+    return lib().eapdtw_version().decode()
+
+
+def _check(rc: int, what: str):
+    if rc != 0:
+        raise EapDtwError(rc, what)
+
+
+def _dev_f32(t, name):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float32:
+        raise TypeError(f"{name} must be a CUDA float32 tensor")
+    if not t.is_contiguous():
+        raise TypeError(f"{name} must be contiguous")
+    return t
+
+
+def _stream_ptr(stream):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def eap_dtw(S, T, w: int | None = None, ub: float = math.inf, out=None, stream=None):
+    """DTW_w(S, T) if <= ub else +inf (Algorithm 3), on raw CUDA float32 series.
+    Returns a 0-d float64 CUDA tensor (asynchronous on the stream)."""
+    import torch
+    S, T = _dev_f32(S, "S"), _dev_f32(T, "T")
+    if w is None:
+        w = max(S.numel(), T.numel())
+    if out is None:
+        out = torch.empty((), dtype=torch.float64, device=S.device)
+    rc = lib().eap_dtw(C.c_void_p(S.data_ptr()), S.numel(), C.c_void_p(T.data_ptr()), T.numel(),
+                       int(w), float(ub), C.c_void_p(out.data_ptr()), _stream_ptr(stream))
+    _check(rc, "eap_dtw")
+    return out
+
+
+def eap_dtw_host(S, T, w: int | None = None, ub: float = math.inf) -> float:
+    S = np.ascontiguousarray(S, dtype=np.float32)
+    T = np.ascontiguousarray(T, dtype=np.float32)
+    if w is None:
+        w = max(len(S), len(T))
+    out = C.c_double(0.0)
+    rc = lib().eap_dtw_host(S.ctypes.data, len(S), T.ctypes.data, len(T), int(w), float(ub),
+                            C.byref(out))
+    _check(rc, "eap_dtw_host")
+    return out.value
+
+
+def _opts(no_lb, tile, no_seed, audit_ub, counters):
+    o = SearchOpts()
+    o.no_lb = int(bool(no_lb))
+    o.tile = int(tile)
+    o.no_seed = int(bool(no_seed))
+    o.audit = int(audit_ub is not None)
+    o.ub_fixed = float(audit_ub) if audit_ub is not None else 0.0
+    o.counters = counters.ctypes.data_as(C.POINTER(C.c_int64))
+    return o
+
+
+def subseq_search(Q, R, w: int, k: int = 1, *, no_lb: bool = False, tile: int = 0,
+                  no_seed: bool = False, audit_ub: float | None = None, out=None, stream=None,
+                  return_counters: bool = False):
+    """k nearest z-normalised subsequences of R to Q under DTW_w (Section 5).
+
+    Q, R: CUDA float32 tensors.  Returns (idx int64[k], dist float64[k]) CUDA
+    tensors, plus a counter dict when return_counters=True.  Blocking."""
+    import torch
+    Q, R = _dev_f32(Q, "Q"), _dev_f32(R, "R")
+    if out is None:
+        idx = torch.empty(k, dtype=torch.int64, device=Q.device)
+        dist = torch.empty(k, dtype=torch.float64, device=Q.device)
+    else:
+        idx, dist = out
+    cnt = np.zeros(NCOUNTERS, dtype=np.int64)
+    o = _opts(no_lb, tile, no_seed, audit_ub, cnt)
+    rc = lib().subseq_search_ex(C.c_void_p(Q.data_ptr()), Q.numel(), C.c_void_p(R.data_ptr()),
+                                R.numel(), int(w), int(k), C.byref(o), C.c_void_p(idx.data_ptr()),
+                                C.c_void_p(dist.data_ptr()), _stream_ptr(stream))
+    _check(rc, "subseq_search")
+    if return_counters:
+        return idx, dist, dict(zip(COUNTER_NAMES, (int(c) for c in cnt)))
+    return idx, dist
+
+
+def subseq_search_host(Q, R, w: int, k: int = 1, *, no_lb: bool = False, tile: int = 0,
+                       no_seed: bool = False, audit_ub: float | None = None,
+                       return_counters: bool = False):
+    """subseq_search on host (numpy) arrays: copies in, searches, copies out."""
+    Q = np.ascontiguousarray(Q, dtype=np.float32)
+    R = np.ascontiguousarray(R, dtype=np.float32)
+    idx = np.empty(k, dtype=np.int64)
+    dist = np.empty(k, dtype=np.float64)
+    cnt = np.zeros(NCOUNTERS, dtype=np.int64)
+    o = _opts(no_lb, tile, no_seed, audit_ub, cnt)
+    rc = lib().subseq_search_host(Q.ctypes.data, len(Q), R.ctypes.data, len(R), int(w), int(k),
+                                  C.byref(o), idx.ctypes.data, dist.ctypes.data)
+    _check(rc, "subseq_search_host")
+    if return_counters:
+        return idx, dist, dict(zip(COUNTER_NAMES, (int(c) for c in cnt)))
+    return idx, dist
+
+
+def release_scratch():
+    _check(lib().eapdtw_release_scratch(), "eapdtw_release_scratch")

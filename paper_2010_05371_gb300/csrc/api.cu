@@ -1,0 +1,478 @@
+// C ABI of the library (declared in include/eapdtw.h): argument checks, scratch
+// management and the launch sequence of eap_dtw and subseq_search.
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "eapdtw.h"
+#include "kernels.h"
+#include "search_kernel.cuh"
+
+using namespace eapdtw;
+
+namespace {
+
+constexpr int kMaxLevels = 4;
+constexpr int kSeedSamples = 4096;
+constexpr int kSeedBest = 32;
+constexpr float kLbScale = 1.0001f;   // prune iff lb > ub * kLbScale (FP32 rounding margin)
+
+// Work levels: the first launch uses K cells per lane; windows whose live
+// region overflows the warp's window of 32 blocks are re-run with 2K, up to 32.
+struct Plan {
+    int nlev = 0;
+    int K[kMaxLevels];
+    int band[kMaxLevels];
+};
+
+Plan plan_levels(int64_t nr, int64_t nc, int64_t w, int tile_hint) {
+    const int64_t lmax = nr > nc ? nr : nc;
+    const bool unconstrained = w >= lmax - 1;
+    int k0 = 32;
+    if (tile_hint == 4 || tile_hint == 8 || tile_hint == 16 || tile_hint == 32) {
+        k0 = tile_hint;
+    } else if (!unconstrained) {
+        // blocks spanned by the band across the pipelined rows, plus margin
+        for (int K = 4; K <= 32; K *= 2)
+            if ((2 * w + K) / (K + 1) + 3 <= 32) { k0 = K; break; }
+    } else {
+        k0 = 8;
+        for (int K = 4; K <= 8; K *= 2)
+            if (32 * K >= nc) { k0 = K; break; }
+    }
+    Plan p;
+    for (int K = k0; K <= 32; K *= 2) {
+        p.K[p.nlev] = K;
+        p.band[p.nlev] = unconstrained ? 0 : (K <= 2 * w + 2 ? 1 : 2);
+        ++p.nlev;
+    }
+    return p;
+}
+
+float ub_to_f32_up(double ub) {
+    if (std::isinf(ub)) return ub > 0 ? INFINITY : -INFINITY;
+    float f = static_cast<float>(ub);
+    if (static_cast<double>(f) < ub) f = std::nextafter(f, INFINITY);
+    return f;
+}
+
+// Device-side scratch of one device, grown on demand.
+struct Scratch {
+    int device = -1;
+    std::mutex mu;
+    // reference statistics
+    double *P1 = nullptr, *P2 = nullptr, *T1 = nullptr, *T2 = nullptr;
+    float* A = nullptr;
+    int64_t cap_n = 0;
+    float *UR = nullptr, *LR = nullptr;
+    int64_t cap_env = 0;
+    // query
+    float *zq = nullptr, *uq = nullptr, *lq = nullptr, *zqo = nullptr;
+    int* ord = nullptr;
+    int cap_m = 0;
+    // state: slots[64] | counters[16] | seed counters[16] | ints[32] | ub_seed
+    unsigned char* state = nullptr;
+    unsigned char* host_state = nullptr;  // pinned copy of counters, seed counters, ints
+    // seed
+    float* seed_ed = nullptr;
+    int* seed_idx = nullptr;
+    int* seed_best = nullptr;
+    // overflow lists
+    int* ovf[2] = {nullptr, nullptr};
+    int cap_ovf = 0;
+    // host-pointer entry points
+    float *dQ = nullptr, *dR = nullptr;
+    int64_t cap_dq = 0, cap_dr = 0;
+    int64_t* dIdx = nullptr;
+    double* dDist = nullptr;
+
+    unsigned long long* slots() { return reinterpret_cast<unsigned long long*>(state); }
+    unsigned long long* counters() { return reinterpret_cast<unsigned long long*>(state + 512); }
+    unsigned long long* seed_counters() { return reinterpret_cast<unsigned long long*>(state + 640); }
+    int* ints() { return reinterpret_cast<int*>(state + 768); }
+    float* ub_seed() { return reinterpret_cast<float*>(state + 896); }
+};
+
+enum IntSlot : int {
+    kWork0 = 0,      // work counters of levels 0..3
+    kWorkSeed = 4,
+    kOvf0 = 5,       // overflow counts written by levels 0..3
+    kBad = 9,
+    kNBest = 10,
+    kSeedOvf = 11,
+    kNumInts = 32
+};
+
+// (Re)allocate p with room for n elements (previous contents are dropped).
+template <typename T>
+bool alloc(T*& p, int64_t n) {
+    if (p) cudaFree(p);
+    p = nullptr;
+    if (cudaMalloc(reinterpret_cast<void**>(&p), sizeof(T) * static_cast<size_t>(n)) != cudaSuccess) {
+        cudaGetLastError();
+        p = nullptr;
+        return false;
+    }
+    return true;
+}
+
+template <typename T>
+void release(T*& p) {
+    if (p) cudaFree(p);
+    p = nullptr;
+}
+
+std::mutex g_mu;
+Scratch* g_scratch[64] = {nullptr};
+
+Scratch* scratch_for_current_device(int* dev_out) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+    *dev_out = dev;
+    std::lock_guard<std::mutex> g(g_mu);
+    if (!g_scratch[dev]) {
+        Scratch* s = new (std::nothrow) Scratch();
+        if (!s) return nullptr;
+        s->device = dev;
+        if (cudaMalloc(reinterpret_cast<void**>(&s->state), 1024) != cudaSuccess ||
+            cudaMallocHost(reinterpret_cast<void**>(&s->host_state), 1024) != cudaSuccess ||
+            cudaMalloc(reinterpret_cast<void**>(&s->seed_ed), sizeof(float) * kSeedSamples) != cudaSuccess ||
+            cudaMalloc(reinterpret_cast<void**>(&s->seed_idx), sizeof(int) * kSeedSamples) != cudaSuccess ||
+            cudaMalloc(reinterpret_cast<void**>(&s->seed_best), sizeof(int) * 64) != cudaSuccess) {
+            cudaGetLastError();
+            delete s;
+            return nullptr;
+        }
+        g_scratch[dev] = s;
+    }
+    return g_scratch[dev];
+}
+
+int32_t cuda_status(cudaError_t e) { return e == cudaSuccess ? EAPDTW_OK : EAPDTW_ERR_CUDA; }
+
+#define CK(expr)                                     \
+    do {                                             \
+        cudaError_t e_ = (expr);                     \
+        if (e_ != cudaSuccess) {                     \
+            cudaGetLastError();                      \
+            return EAPDTW_ERR_CUDA;                  \
+        }                                            \
+    } while (0)
+
+int32_t search_impl(Scratch& S, const float* Q, int64_t lQ, const float* R, int64_t lR, int64_t w,
+                    int32_t k, const eapdtw_search_opts* opts, int64_t* out_idx, double* out_dist,
+                    cudaStream_t st) {
+    const int m = static_cast<int>(lQ);
+    const int64_t n = lR;
+    const int64_t nw = n - m + 1;
+    const int wi = static_cast<int>(w < m ? w : m);   // w >= m - 1 is unconstrained
+    const bool use_lb = !(opts && opts->no_lb);
+    const bool seed = !(opts && opts->no_seed) && nw >= 2048;
+    const bool audit = opts && opts->audit;
+    if (audit && std::isnan(opts->ub_fixed)) return EAPDTW_ERR_INVALID_ARG;
+    if (search_warps(m) < 1) return EAPDTW_ERR_UNSUPPORTED;
+    const Plan plan = plan_levels(m, m, wi, opts ? opts->tile : 0);
+
+    // scratch
+    if (S.cap_n < n) {
+        const int64_t ncap = (n + kChunk - 1) / kChunk;
+        S.cap_n = 0;
+        if (!alloc(S.P1, n) || !alloc(S.P2, n) || !alloc(S.T1, ncap) || !alloc(S.T2, ncap) ||
+            !alloc(S.A, ncap))
+            return EAPDTW_ERR_OUT_OF_MEMORY;
+        S.cap_n = n;
+    }
+    if (use_lb && S.cap_env < n) {
+        S.cap_env = 0;
+        if (!alloc(S.UR, n) || !alloc(S.LR, n)) return EAPDTW_ERR_OUT_OF_MEMORY;
+        S.cap_env = n;
+    }
+    const int mp = query_pad(m);
+    if (S.cap_m < mp) {
+        S.cap_m = 0;
+        if (!alloc(S.zq, mp) || !alloc(S.uq, mp) || !alloc(S.lq, mp) || !alloc(S.zqo, mp) ||
+            !alloc(S.ord, mp))
+            return EAPDTW_ERR_OUT_OF_MEMORY;
+        S.cap_m = mp;
+    }
+    const int want_ovf = static_cast<int>(nw < (1 << 22) ? nw : (1 << 22));
+    if (S.cap_ovf < want_ovf) {
+        S.cap_ovf = 0;
+        if (!alloc(S.ovf[0], want_ovf) || !alloc(S.ovf[1], want_ovf)) return EAPDTW_ERR_OUT_OF_MEMORY;
+        S.cap_ovf = want_ovf;
+    }
+
+    int* ints = S.ints();
+    CK(launch_init_state(S.slots(), k, S.ub_seed(), S.counters(), ints, kNumInts, st));
+    CK(cudaMemsetAsync(S.seed_counters(), 0, 128, st));
+    CK(launch_ref_prefix(R, n, S.P1, S.P2, S.T1, S.T2, S.A, ints + kBad, st));
+    CK(launch_query_prep(Q, m, wi, S.zq, S.uq, S.lq, S.zqo, S.ord, ints + kBad, st));
+    if (use_lb) CK(launch_envelope(R, n, wi < m - 1 ? wi : m - 1, S.UR, S.LR, st));
+
+    SearchArgs a{};
+    a.ref = RefView{R, n, S.P1, S.P2, S.T1, S.T2, S.A};
+    a.q = QueryView{S.zq, S.uq, S.lq, S.zqo, S.ord, m};
+    a.ur = S.UR;
+    a.lr = S.LR;
+    a.bsf = BestSoFar{S.slots(), S.ub_seed(), k, audit ? 1 : 0,
+                      audit ? ub_to_f32_up(opts->ub_fixed) : 0.0f};
+    a.nw = nw;
+    a.w = wi;
+    a.use_lb = use_lb ? 1 : 0;
+    a.lb_scale = kLbScale;
+    a.counters = S.counters();
+
+    if (seed && !audit) {
+        const int ns = static_cast<int>(nw < kSeedSamples ? nw : kSeedSamples);
+        CK(launch_seed(a.ref, S.zq, m, nw, ns, S.seed_ed, S.seed_idx, k, S.ub_seed(), S.seed_best,
+                       kSeedBest, ints + kNBest, st));
+        SearchArgs sa = a;
+        sa.use_lb = 0;
+        sa.work_counter = ints + kWorkSeed;
+        sa.ovf_in = S.seed_best;
+        sa.ovf_in_count = ints + kNBest;
+        sa.ovf_in_cap = kSeedBest;
+        sa.ovf_out = nullptr;
+        sa.ovf_out_count = ints + kSeedOvf;
+        sa.ovf_cap = 0;
+        sa.counters = S.seed_counters();  // kept apart from the search's own counts
+        const int K = plan.K[plan.nlev - 1];
+        CK(launch_search(K, plan.band[plan.nlev - 1], sa, search_blocks(K, plan.band[plan.nlev - 1], m) / 4 + 1, st));
+    }
+    for (int lev = 0; lev < plan.nlev; ++lev) {
+        SearchArgs la = a;
+        la.work_counter = ints + kWork0 + lev;
+        la.ovf_out = S.ovf[lev & 1];
+        la.ovf_out_count = ints + kOvf0 + lev;
+        la.ovf_cap = S.cap_ovf;
+        if (lev > 0) {
+            la.ovf_in = S.ovf[(lev - 1) & 1];
+            la.ovf_in_count = ints + kOvf0 + lev - 1;
+            la.ovf_in_cap = S.cap_ovf;
+        }
+        CK(launch_search(plan.K[lev], plan.band[lev], la, search_blocks(plan.K[lev], plan.band[lev], m), st));
+    }
+    CK(launch_finalize(S.slots(), k, out_idx, out_dist, st));
+    CK(cudaMemcpyAsync(S.host_state, S.state + 512, 384, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    const unsigned long long* hc = reinterpret_cast<const unsigned long long*>(S.host_state);
+    const int* hi = reinterpret_cast<const int*>(S.host_state + 256);
+    if (opts && opts->counters) {
+        for (int c = 0; c < EAPDTW_NCOUNTERS; ++c) opts->counters[c] = static_cast<int64_t>(hc[c]);
+    }
+    if (hi[kBad]) return EAPDTW_ERR_NAN_INPUT;
+    for (int lev = 0; lev + 1 < plan.nlev; ++lev)
+        if (hi[kOvf0 + lev] > S.cap_ovf) return EAPDTW_ERR_INTERNAL;
+    if (hi[kOvf0 + plan.nlev - 1] > 0) return EAPDTW_ERR_UNSUPPORTED;
+    return EAPDTW_OK;
+}
+
+int32_t check_search_args(const float* Q, int64_t lQ, const float* R, int64_t lR, int64_t w,
+                          int32_t k, const void* out_idx, const void* out_dist) {
+    if (!Q || !R || !out_idx || !out_dist) return EAPDTW_ERR_INVALID_ARG;
+    if (lQ < 1 || lR < lQ || w < 0 || k < 1) return EAPDTW_ERR_INVALID_ARG;
+    if (lQ > EAPDTW_MAX_QUERY || k > EAPDTW_MAX_K || lR >= (int64_t(1) << 31))
+        return EAPDTW_ERR_UNSUPPORTED;
+    return EAPDTW_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* eapdtw_strerror(int32_t code) {
+    switch (code) {
+        case EAPDTW_OK: return "ok";
+        case EAPDTW_ERR_INVALID_ARG: return "invalid argument";
+        case EAPDTW_ERR_NAN_INPUT: return "NaN or Inf in an input series";
+        case EAPDTW_ERR_OUT_OF_MEMORY: return "out of device memory";
+        case EAPDTW_ERR_CUDA: return "CUDA runtime error";
+        case EAPDTW_ERR_TIMEOUT: return "device wait timed out";
+        case EAPDTW_ERR_UNSUPPORTED: return "size not supported by this build";
+        case EAPDTW_ERR_INTERNAL: return "internal consistency check failed";
+        default: return "unknown error code";
+    }
+}
+
+const char* eapdtw_version(void) { return "eapdtw-gb300 0.1 (sm_103a)"; }
+
+int32_t eap_dtw(const float* S, int64_t lS, const float* T, int64_t lT, int64_t w, double ub,
+                double* out_dist, void* stream) {
+    if (!S || !T || !out_dist || lS < 1 || lT < 1 || w < 0 || std::isnan(ub))
+        return EAPDTW_ERR_INVALID_ARG;
+    const bool t_rows = lT > lS;  // rows = longer series; ties: rows = S
+    const float* rows = t_rows ? T : S;
+    const float* cols = t_rows ? S : T;
+    const int64_t nr = t_rows ? lT : lS;
+    const int64_t nc = t_rows ? lS : lT;
+    if (nc > EAPDTW_MAX_PAIR_COLS || nr >= (int64_t(1) << 30)) return EAPDTW_ERR_UNSUPPORTED;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    CK(cudaMemsetAsync(out_dist, 0xff, sizeof(double), st));  // NaN until a level succeeds
+    if (w < nr - nc) {
+        // no admissible warping path
+        const double inf = INFINITY;
+        CK(cudaMemcpyAsync(out_dist, &inf, sizeof(double), cudaMemcpyHostToDevice, st));
+        CK(cudaStreamSynchronize(st));
+        return EAPDTW_OK;
+    }
+    const int64_t lmax = nr;
+    const int wi = static_cast<int>(w < lmax ? w : lmax);
+    const Plan plan = plan_levels(nr, nc, wi, 0);
+    const float ubf = ub_to_f32_up(ub);
+    for (int lev = 0; lev < plan.nlev; ++lev)
+        CK(launch_pair(plan.K[lev], plan.band[lev], rows, static_cast<int>(nr), cols,
+                       static_cast<int>(nc), wi, ubf, out_dist, nullptr, lev == plan.nlev - 1, st));
+    return EAPDTW_OK;
+}
+
+int32_t eap_dtw_host(const float* S, int64_t lS, const float* T, int64_t lT, int64_t w, double ub,
+                     double* out_dist) {
+    if (!S || !T || !out_dist || lS < 1 || lT < 1 || w < 0 || std::isnan(ub))
+        return EAPDTW_ERR_INVALID_ARG;
+    float *dS = nullptr, *dT = nullptr;
+    double* dOut = nullptr;
+    int32_t rc = EAPDTW_OK;
+    if (cudaMalloc(reinterpret_cast<void**>(&dS), sizeof(float) * lS) != cudaSuccess ||
+        cudaMalloc(reinterpret_cast<void**>(&dT), sizeof(float) * lT) != cudaSuccess ||
+        cudaMalloc(reinterpret_cast<void**>(&dOut), sizeof(double)) != cudaSuccess) {
+        cudaGetLastError();
+        rc = EAPDTW_ERR_OUT_OF_MEMORY;
+    }
+    if (rc == EAPDTW_OK &&
+        (cudaMemcpy(dS, S, sizeof(float) * lS, cudaMemcpyHostToDevice) != cudaSuccess ||
+         cudaMemcpy(dT, T, sizeof(float) * lT, cudaMemcpyHostToDevice) != cudaSuccess))
+        rc = EAPDTW_ERR_CUDA;
+    if (rc == EAPDTW_OK) rc = eap_dtw(dS, lS, dT, lT, w, ub, dOut, nullptr);
+    if (rc == EAPDTW_OK &&
+        cudaMemcpy(out_dist, dOut, sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess)
+        rc = EAPDTW_ERR_CUDA;
+    if (rc == EAPDTW_OK && std::isnan(*out_dist)) rc = EAPDTW_ERR_UNSUPPORTED;
+    cudaFree(dS);
+    cudaFree(dT);
+    cudaFree(dOut);
+    cudaGetLastError();
+    return rc;
+}
+
+int32_t subseq_search_ex(const float* Q, int64_t lQ, const float* R, int64_t lR, int64_t w,
+                         int32_t k, const eapdtw_search_opts* opts, int64_t* out_idx,
+                         double* out_dist, void* stream) {
+    int32_t rc = check_search_args(Q, lQ, R, lR, w, k, out_idx, out_dist);
+    if (rc != EAPDTW_OK) return rc;
+    int dev = 0;
+    Scratch* S = scratch_for_current_device(&dev);
+    if (!S) return EAPDTW_ERR_OUT_OF_MEMORY;
+    std::lock_guard<std::mutex> g(S->mu);
+    try {
+        return search_impl(*S, Q, lQ, R, lR, w, k, opts, out_idx, out_dist,
+                           static_cast<cudaStream_t>(stream));
+    } catch (...) {
+        return EAPDTW_ERR_INTERNAL;
+    }
+}
+
+int32_t subseq_search(const float* Q, int64_t lQ, const float* R, int64_t lR, int64_t w,
+                      int32_t k, int64_t* out_idx, double* out_dist, void* stream) {
+    return subseq_search_ex(Q, lQ, R, lR, w, k, nullptr, out_idx, out_dist, stream);
+}
+
+int32_t subseq_search_host(const float* Q, int64_t lQ, const float* R, int64_t lR, int64_t w,
+                           int32_t k, const eapdtw_search_opts* opts, int64_t* out_idx,
+                           double* out_dist) {
+    int32_t rc = check_search_args(Q, lQ, R, lR, w, k, out_idx, out_dist);
+    if (rc != EAPDTW_OK) return rc;
+    int dev = 0;
+    Scratch* S = scratch_for_current_device(&dev);
+    if (!S) return EAPDTW_ERR_OUT_OF_MEMORY;
+    std::lock_guard<std::mutex> g(S->mu);
+    if (S->cap_dq < lQ) {
+        S->cap_dq = 0;
+        if (!alloc(S->dQ, lQ)) return EAPDTW_ERR_OUT_OF_MEMORY;
+        S->cap_dq = lQ;
+    }
+    if (S->cap_dr < lR) {
+        S->cap_dr = 0;
+        if (!alloc(S->dR, lR)) return EAPDTW_ERR_OUT_OF_MEMORY;
+        S->cap_dr = lR;
+    }
+    if (!S->dIdx) {
+        if (cudaMalloc(reinterpret_cast<void**>(&S->dIdx), sizeof(int64_t) * EAPDTW_MAX_K) != cudaSuccess ||
+            cudaMalloc(reinterpret_cast<void**>(&S->dDist), sizeof(double) * EAPDTW_MAX_K) != cudaSuccess) {
+            cudaGetLastError();
+            return EAPDTW_ERR_OUT_OF_MEMORY;
+        }
+    }
+    cudaStream_t st = nullptr;
+    CK(cudaMemcpyAsync(S->dQ, Q, sizeof(float) * lQ, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(S->dR, R, sizeof(float) * lR, cudaMemcpyHostToDevice, st));
+    try {
+        rc = search_impl(*S, S->dQ, lQ, S->dR, lR, w, k, opts, S->dIdx, S->dDist, st);
+    } catch (...) {
+        rc = EAPDTW_ERR_INTERNAL;
+    }
+    if (rc != EAPDTW_OK) return rc;
+    CK(cudaMemcpyAsync(out_idx, S->dIdx, sizeof(int64_t) * k, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(out_dist, S->dDist, sizeof(double) * k, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    return EAPDTW_OK;
+}
+
+int32_t eapdtw_release_scratch(void) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return EAPDTW_ERR_CUDA;
+    std::lock_guard<std::mutex> g(g_mu);
+    Scratch* S = (dev >= 0 && dev < 64) ? g_scratch[dev] : nullptr;
+    if (!S) return EAPDTW_OK;
+    {
+        std::lock_guard<std::mutex> g2(S->mu);
+        release(S->P1); release(S->P2); release(S->T1); release(S->T2); release(S->A);
+        release(S->UR); release(S->LR);
+        release(S->zq); release(S->uq); release(S->lq); release(S->zqo); release(S->ord);
+        release(S->ovf[0]); release(S->ovf[1]);
+        release(S->dQ); release(S->dR); release(S->dIdx); release(S->dDist);
+        release(S->state); release(S->seed_ed); release(S->seed_idx); release(S->seed_best);
+        if (S->host_state) cudaFreeHost(S->host_state);
+        S->host_state = nullptr;
+    }
+    delete S;
+    g_scratch[dev] = nullptr;
+    return EAPDTW_OK;
+}
+
+}  // extern "C"
+
+namespace eapdtw {
+
+cudaError_t launch_search_k4(int band, const SearchArgs& args, int blocks, cudaStream_t s);
+cudaError_t launch_search_k8(int band, const SearchArgs& args, int blocks, cudaStream_t s);
+cudaError_t launch_search_k16(int band, const SearchArgs& args, int blocks, cudaStream_t s);
+cudaError_t launch_search_k32(int band, const SearchArgs& args, int blocks, cudaStream_t s);
+int search_blocks_k4(int band, int m);
+int search_blocks_k8(int band, int m);
+int search_blocks_k16(int band, int m);
+int search_blocks_k32(int band, int m);
+
+cudaError_t launch_search(int K, int band, const SearchArgs& args, int blocks, cudaStream_t s) {
+    switch (K) {
+        case 4: return launch_search_k4(band, args, blocks, s);
+        case 8: return launch_search_k8(band, args, blocks, s);
+        case 16: return launch_search_k16(band, args, blocks, s);
+        default: return launch_search_k32(band, args, blocks, s);
+    }
+}
+
+int search_blocks(int K, int band, int m) {
+    switch (K) {
+        case 4: return search_blocks_k4(band, m);
+        case 8: return search_blocks_k8(band, m);
+        case 16: return search_blocks_k16(band, m);
+        default: return search_blocks_k32(band, m);
+    }
+}
+
+}  // namespace eapdtw

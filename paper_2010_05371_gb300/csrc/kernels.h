@@ -1,0 +1,36 @@
+// Host-side launchers shared between the CUDA translation units of the library.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace eapdtw {
+
+struct SearchArgs;
+
+cudaError_t launch_ref_prefix(const float* R, int64_t n, double* P1, double* P2, double* T1,
+                              double* T2, float* A, int* bad, cudaStream_t s);
+cudaError_t launch_query_prep(const float* Q, int m, int w, float* zq, float* uq_o, float* lq_o,
+                              float* zq_o, int* ord, int* bad, cudaStream_t s);
+cudaError_t launch_envelope(const float* R, int64_t n, int w, float* U, float* L, cudaStream_t s);
+cudaError_t launch_init_state(unsigned long long* slots, int k, float* ub_seed,
+                              unsigned long long* counters, int* ints, int nints, cudaStream_t s);
+cudaError_t launch_seed(const RefView& ref, const float* zq, int m, int64_t nw, int nsamples,
+                        float* ed, int* idx, int k, float* ub_seed, int* best, int nbest,
+                        int* nbest_out, cudaStream_t s);
+cudaError_t launch_finalize(const unsigned long long* slots, int k, int64_t* out_idx,
+                            double* out_dist, cudaStream_t s);
+
+// search_kernel<K, BAND> for K in {4, 8, 16, 32} and BAND in {0, 1, 2}; one
+// translation unit per K.  blocks = 0 picks a persistent grid from occupancy.
+cudaError_t launch_search(int K, int band, const SearchArgs& args, int blocks, cudaStream_t s);
+int search_blocks(int K, int band, int m);
+
+// eap_dtw single pair: one warp.
+cudaError_t launch_pair(int K, int band, const float* rows, int nr, const float* cols, int nc, int w,
+                        float ub, double* out, int* ovf_flag, int final_level, cudaStream_t s);
+
+}  // namespace eapdtw

@@ -1,0 +1,249 @@
+// Subsequence search kernel: the UCR-Suite loop of Section 5 run over all
+// candidate windows in parallel (sm_103a).
+//
+// Persistent warps take tiles of 32 consecutive windows from a global counter.
+//  1. The warp streams R[i0 .. i0+31+m) into its shared-memory tile with
+//     coalesced 16-byte loads.
+//  2. Lane l owns window i0 + l: window statistics from the chunk-anchored
+//     prefix sums, then LB_Kim (first/last points), LB_Keogh EQ (window vs
+//     query envelope) and LB_Keogh EC (query vs the window's normalised
+//     reference envelope), each skipping the window if above the current
+//     upper bound (Section 2.2).  Terms are visited in decreasing |zq| order
+//     with early exit every 8 terms.
+//  3. Surviving windows are run one after another by the whole warp through
+//     the EAPrunedDTW wavefront (dtw_wavefront.cuh) against the current k-th
+//     best distance, re-read every few steps; a value <= ub enters the k-best
+//     list by atomicMin.
+// List mode (ovf_in != nullptr) re-runs single windows whose live region did
+// not fit the window of blocks of a narrower launch.
+#pragma once
+
+#include "common.cuh"
+#include "dtw_wavefront.cuh"
+
+namespace eapdtw {
+
+constexpr int kWarpsPerBlock = 8;
+constexpr int kLbUnroll = 8;
+
+struct SearchArgs {
+    RefView ref;
+    QueryView q;
+    const float* ur;   // reference envelope (upper) over +-w_env, raw values [n]
+    const float* lr;   // lower
+    BestSoFar bsf;
+    int64_t nw;        // number of windows n - m + 1
+    int w;             // warping window
+    int use_lb;
+    float lb_scale;    // prune iff lb > ub * lb_scale (lb_scale = 1 + slack)
+    int* work_counter; // tile / list-item counter
+    unsigned long long* counters;
+    int* ovf_out;      // windows whose live region overflowed (re-run wider)
+    int* ovf_out_count;
+    int ovf_cap;
+    const int* ovf_in;        // list mode input
+    const int* ovf_in_count;
+    int ovf_in_cap;           // entries beyond the capacity were dropped by the producer
+};
+
+__host__ __device__ inline int query_pad(int m) { return (m + kLbUnroll - 1) / kLbUnroll * kLbUnroll; }
+__host__ __device__ inline int tile_floats(int m) { return (m + 31 + 3) / 4 * 4 + 4; }
+
+// Warps per block: up to kWarpsPerBlock, fewer when long queries fill shared memory.
+__host__ inline int search_warps(int m) {
+    const size_t budget = 227 * 1024;
+    const size_t q = sizeof(float) * 5 * static_cast<size_t>(query_pad(m));
+    const size_t t = sizeof(float) * static_cast<size_t>(tile_floats(m));
+    if (q + t > budget) return 0;
+    size_t w = (budget - q) / t;
+    return static_cast<int>(w < kWarpsPerBlock ? w : kWarpsPerBlock);
+}
+
+__host__ inline size_t search_smem_bytes(int m) {
+    const int mp = query_pad(m);
+    return sizeof(float) * (5 * static_cast<size_t>(mp) + search_warps(m) * static_cast<size_t>(tile_floats(m)));
+}
+
+template <int K, int BAND>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32)
+search_kernel(const SearchArgs A) {
+    extern __shared__ __align__(16) float smem[];
+    const int m = A.q.m;
+    const int mp = query_pad(m);
+    float* s_zq = smem;
+    float* s_uq = s_zq + mp;
+    float* s_lq = s_uq + mp;
+    float* s_zqo = s_lq + mp;
+    int* s_ord = reinterpret_cast<int*>(s_zqo + mp);
+    const int warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
+    float* s_r = reinterpret_cast<float*>(s_ord + mp) + warp * tile_floats(m);
+
+    for (int j = threadIdx.x; j < mp; j += blockDim.x) {
+        s_zq[j] = j < m ? A.q.zq[j] : f_nan();
+        s_uq[j] = A.q.uq_o[j];
+        s_lq[j] = A.q.lq_o[j];
+        s_zqo[j] = A.q.zq_o[j];
+        s_ord[j] = A.q.ord[j];
+    }
+    __syncthreads();
+
+    const bool list_mode = A.ovf_in != nullptr;
+    const int64_t n = A.ref.n;
+    int64_t nitems = (A.nw + 31) / 32;
+    if (list_mode) {
+        const int c = *A.ovf_in_count;
+        nitems = c < A.ovf_in_cap ? c : A.ovf_in_cap;
+    }
+    const bool r_aligned = (reinterpret_cast<uintptr_t>(A.ref.R) & 15) == 0;
+    // per-lane counters (summed over the warp at the end)
+    unsigned long long c_win = 0, c_kim = 0, c_eq = 0, c_ec = 0;
+    unsigned long long c_ab = 0, c_done = 0, c_cells = 0, c_re = 0, c_ovf = 0, c_steps = 0;
+
+    for (;;) {
+        int item = 0;
+        if (lane == 0) item = atomicAdd(A.work_counter, 1);
+        item = __shfl_sync(kFull, item, 0);
+        if (item >= nitems) break;
+
+        int64_t i0;
+        int nlanes;  // windows in this work item
+        if (!list_mode) {
+            i0 = static_cast<int64_t>(item) * 32;
+            nlanes = static_cast<int>(A.nw - i0 < 32 ? A.nw - i0 : 32);
+        } else {
+            i0 = A.ovf_in[item];
+            nlanes = 1;
+        }
+        // Stage R[i0 .. i0 + nlanes - 1 + m) into the warp's tile.
+        const int len = nlanes - 1 + m;
+        if (r_aligned && !list_mode) {
+            const float4* src = reinterpret_cast<const float4*>(A.ref.R + i0);
+            const int nv = len / 4;
+            for (int v = lane; v < nv; v += 32) reinterpret_cast<float4*>(s_r)[v] = __ldg(src + v);
+            for (int j = nv * 4 + lane; j < len; j += 32) s_r[j] = __ldg(A.ref.R + i0 + j);
+        } else {
+            for (int j = lane; j < len; j += 32) s_r[j] = __ldg(A.ref.R + i0 + j);
+        }
+        __syncwarp();
+
+        // ---- per-lane window statistics and lower bounds ------------------
+        const int my = list_mode ? 0 : lane;
+        const bool valid = lane < nlanes || list_mode;
+        const int64_t i = i0 + my;
+        float a = 0.0f, cw = 0.0f, isd = 0.0f;
+        if (valid) window_coeffs(A.ref, i, m, s_r + my, a, cw, isd);
+        float lb = 0.0f;
+        bool alive = valid && (!list_mode || lane == 0);
+        if (!list_mode && lane < nlanes) c_win++;
+        if (A.use_lb && alive && !list_mode) {
+            const float ub = A.bsf.load() * A.lb_scale;
+            const float* x = s_r + my;
+            const float z0 = znorm1(x[0], a, cw, isd);
+            const float d0 = __fsub_rn(z0, s_zq[0]);
+            float kim = __fmul_rn(d0, d0);
+            if (m > 1) {
+                const float dl = __fsub_rn(znorm1(x[m - 1], a, cw, isd), s_zq[m - 1]);
+                kim = __fmaf_rn(dl, dl, kim);
+            }
+            lb = kim;
+            if (kim > ub) {
+                alive = false;
+                c_kim++;
+            } else {
+                // LB_Keogh EQ: the normalised window against the query envelope.
+                float s = 0.0f;
+                for (int p = 0; p < mp; p += kLbUnroll) {
+#pragma unroll
+                    for (int u = 0; u < kLbUnroll; ++u) {
+                        const int j = s_ord[p + u];
+                        const float z = znorm1(x[j], a, cw, isd);
+                        const float e = fmaxf(fmaxf(__fsub_rn(z, s_uq[p + u]), __fsub_rn(s_lq[p + u], z)), 0.0f);
+                        s = __fmaf_rn(e, e, s);
+                    }
+                    if (s > ub) break;
+                }
+                lb = fmaxf(lb, s);
+                if (s > ub) {
+                    alive = false;
+                    c_eq++;
+                } else {
+                    // LB_Keogh EC: the query against the window's envelope.
+                    float s2 = 0.0f;
+                    const float* ur = A.ur + i;
+                    const float* lr = A.lr + i;
+                    for (int p = 0; p < mp; p += kLbUnroll) {
+#pragma unroll
+                        for (int u = 0; u < kLbUnroll; ++u) {
+                            const int j = s_ord[p + u];
+                            const float uu = znorm1(__ldg(ur + j), a, cw, isd);
+                            const float ll = znorm1(__ldg(lr + j), a, cw, isd);
+                            const float qv = s_zqo[p + u];
+                            const float e = fmaxf(fmaxf(__fsub_rn(qv, uu), __fsub_rn(ll, qv)), 0.0f);
+                            s2 = __fmaf_rn(e, e, s2);
+                        }
+                        if (s2 > ub) break;
+                    }
+                    lb = fmaxf(lb, s2);
+                    if (s2 > ub) {
+                        alive = false;
+                        c_ec++;
+                    }
+                }
+            }
+        }
+
+        // ---- EAPrunedDTW on the survivors, one warp per window ------------
+        unsigned mask = __ballot_sync(kFull, alive);
+        while (mask) {
+            const int src = __ffs(mask) - 1;
+            mask &= mask - 1;
+            const float a_s = __shfl_sync(kFull, a, src);
+            const float cw_s = __shfl_sync(kFull, cw, src);
+            const float isd_s = __shfl_sync(kFull, isd, src);
+            const float lb_s = __shfl_sync(kFull, lb, src);
+            const int off = list_mode ? 0 : src;
+            const int64_t iw = i0 + off;
+            float ub = A.bsf.load();
+            if (A.use_lb && !list_mode && lb_s > ub * A.lb_scale) {
+                if (lane == 0) c_re++;
+                continue;
+            }
+            const DtwOut o = dtw_warp<K, BAND>(s_r + off, a_s, cw_s, isd_s, s_zq, m, m, A.w, A.bsf, ub);
+            if (lane == 0) {
+                c_steps += static_cast<unsigned long long>(o.steps);
+                c_cells += static_cast<unsigned long long>(o.busy) * K;
+            }
+            if (o.status != 0) {
+                if (lane == 0) {
+                    c_ovf++;
+                    const int slot = atomicAdd(A.ovf_out_count, 1);
+                    if (slot < A.ovf_cap) A.ovf_out[slot] = static_cast<int>(iw);
+                }
+                continue;
+            }
+            ub = A.bsf.load();
+            if (o.dist <= ub) {
+                if (lane == 0) {
+                    A.bsf.insert(o.dist, static_cast<uint32_t>(iw));
+                    c_done++;
+                }
+            } else if (lane == 0) {
+                c_ab++;
+            }
+        }
+        __syncwarp();
+    }
+
+    // warp-sum of the per-lane counters, one atomic per counter per warp
+    unsigned long long v[10] = {c_win, c_kim, c_eq, c_ec, c_ab, c_done, c_cells, c_re, c_ovf, c_steps};
+#pragma unroll
+    for (int c = 0; c < 10; ++c) {
+        unsigned long long x = v[c];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(kFull, x, o);
+        if (lane == 0 && x) atomicAdd(A.counters + c, x);
+    }
+}
+
+}  // namespace eapdtw

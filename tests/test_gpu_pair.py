@@ -1,0 +1,84 @@
+"""eap_dtw (Algorithm 3 on one pair, through the C ABI) against the oracle."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+import pins
+from gpu_util import dist_close
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+from paper_2010_05371_gb300 import api  # noqa: E402
+
+
+def dev(x):
+    return torch.tensor(np.asarray(x, dtype=np.float32), device="cuda")
+
+
+def f32(x):
+    return np.asarray(x, dtype=np.float32).astype(np.float64)
+
+
+def test_worked_example():
+    g = pins.load_golden()
+    S = [float(x) for x in g["S"].split()]
+    T = [float(x) for x in g["T"].split()]
+    assert api.eap_dtw(dev(S), dev(T)).item() == float(g["dtw"])
+    assert api.eap_dtw(dev(S), dev(T), ub=9).item() == float(g["ub9_result"])
+    assert math.isinf(api.eap_dtw(dev(S), dev(T), ub=6).item())
+    assert api.eap_dtw_host(S, T, ub=9) == 9.0
+
+
+def _pair_cases(seed, count, lmax):
+    rng = np.random.default_rng(seed)
+    for c in range(count):
+        n = int(rng.integers(1, lmax + 1))
+        m = n if c % 3 else int(rng.integers(1, lmax + 1))
+        if c % 4 == 0:
+            S = rng.integers(0, 5, n).astype(np.float64)
+            T = rng.integers(0, 5, m).astype(np.float64)
+        else:
+            S = f32(np.cumsum(rng.standard_normal(n)))
+            T = f32(np.cumsum(rng.standard_normal(m)))
+        w = int(rng.integers(0, max(n, m) + 2))
+        yield S, T, w, rng
+
+
+@pytest.mark.parametrize("seed,count,lmax", [(1, 300, 40), (2, 120, 300), (3, 30, 1024)])
+def test_random_pairs(seed, count, lmax):
+    for S, T, w, rng in _pair_cases(seed, count, lmax):
+        d = O.dtw(S, T, w)
+        ubs = [math.inf]
+        if math.isfinite(d):
+            ubs += [d * 0.9, d * 1.1, d * float(rng.uniform(0.3, 3.0))]
+        else:
+            ubs += [1e9]
+        for ub in ubs:
+            got = api.eap_dtw(dev(S), dev(T), w, ub).item()
+            if math.isfinite(d) and abs(d - ub) <= 1e-4 * max(d, 1e-6):
+                continue  # FP32 vs FP64 decides this one
+            exp = d if d <= ub else math.inf
+            assert dist_close(got, exp, max(len(S), len(T))), (len(S), len(T), w, ub, got, exp)
+
+
+def test_no_admissible_path_and_degenerate():
+    assert math.isinf(api.eap_dtw(dev([1, 2, 3, 4, 5]), dev([1, 2]), 2).item())
+    assert api.eap_dtw(dev([1, 2, 3, 4, 5]), dev([1, 2]), 3).item() == O.dtw([1, 2, 3, 4, 5], [1, 2], 3)
+    assert api.eap_dtw(dev([2.5]), dev([0.5]), 0).item() == 4.0
+    x = dev(np.linspace(-1, 1, 200))
+    assert api.eap_dtw(x, x, 5).item() == 0.0
+    assert api.eap_dtw(x, x, 5, ub=0.0).item() == 0.0
+
+
+def test_ties_are_not_abandoned():
+    """A DTW exactly equal to ub is returned (strict > ub abandons, Section 2.2)."""
+    rng = np.random.default_rng(7)
+    for _ in range(50):
+        S = rng.integers(0, 4, 30).astype(np.float64)
+        T = rng.integers(0, 4, 30).astype(np.float64)
+        d = O.dtw(S, T, 5)
+        assert api.eap_dtw(dev(S), dev(T), 5, d).item() == d
+        if d > 0:
+            assert math.isinf(api.eap_dtw(dev(S), dev(T), 5, d - 0.5).item())
