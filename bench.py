@@ -1,0 +1,368 @@
+#!/usr/bin/env python3
+"""Benchmark: candidate windows/s of EAPrunedDTW subsequence search on GB300.
+
+One step = the large workload: a Gaussian random walk of 20,000,000 FP32 points
+(seed 0) searched by four random-walk queries of length 1024 (seeds 1-4), each
+once with w = 103 (10%, LB_Kim -> LB_Keogh EQ -> EC -> EAPrunedDTW) and once
+with w = 1024 (unconstrained, no lower bounds): 8 searches, k = 1.
+
+Prints one JSON line (rank 0).  `value` is whole-job candidate windows/s with
+the inputs resident in HBM; `e2e` is the same metric with the reference and
+queries copied from pinned host memory and the results read back every step.
+`--impl reference` times the CPU oracle on a bounded sample of the same
+workload instead.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+N_DEFAULT = 20_000_000
+M = 1024
+QUERY_SEEDS = (1, 2, 3, 4)
+SEARCHES = [(103, False), (1024, True)]  # (w, no lower bounds)
+METRIC = "candidate windows/s"
+GOLDEN = os.path.join(ROOT, "tests", "golden", "bench_large_oracle.json")
+# Issue slots of the minimal DP cell: d = z - q; min(top, diag); min(., left);
+# fma(d, d, .) -- four FP32-pipe instructions.
+OPS_PER_CELL = 4
+FP32_LANES_PER_SM = 128
+# CPU baseline sample (oracle): windows of the cascade (w=103) and nolb (w=1024) searches
+CPU_SAMPLE = {"cascade_windows": 2_000_000, "nolb_windows": 200_000, "query_seed": 1}
+
+
+def workload_desc(n):
+    return (f"large: random walk n={n} (FP32, seed 0); 4 random-walk queries m={M} (seeds 1-4); "
+            f"each searched with w=103 + LB_Kim/LB_Keogh cascade and with w=1024 (unconstrained, "
+            f"no lower bounds); k=1")
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", self.gpu_id, f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except (OSError, ValueError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        return False
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def load_golden(n):
+    try:
+        with open(GOLDEN) as f:
+            g = json.load(f)
+    except (OSError, ValueError):
+        return None
+    if f"n={n}" not in g.get("workload", ""):
+        return None
+    want = {(s, w, not nolb) for s in QUERY_SEEDS for (w, nolb) in SEARCHES}
+    have = {(e["query_seed"], e["w"], e["lower_bounds"]): e for e in g.get("searches", [])}
+    if not want.issubset(have):
+        return None
+    return have
+
+
+def cpu_baseline(n_threads=None):
+    """The oracle (FP64 C cascade) on a bounded sample of the workload."""
+    import oracle as O
+    from paper_2010_05371_gb300 import synth
+    nt = n_threads or os.cpu_count() or 1
+    Q = synth.random_walk(M, CPU_SAMPLE["query_seed"])
+    nc, nn = CPU_SAMPLE["cascade_windows"], CPU_SAMPLE["nolb_windows"]
+    R = synth.random_walk(max(nc, nn) + M - 1, 0)
+    t0 = time.perf_counter()
+    O.search_cascade(Q, R[:nc + M - 1], 103, 1, use_lb=True, nthreads=nt)
+    t1 = time.perf_counter()
+    O.search_cascade(Q, R[:nn + M - 1], 1024, 1, use_lb=False, nthreads=nt)
+    t2 = time.perf_counter()
+    rate_c, rate_n = nc / (t1 - t0), nn / (t2 - t1)
+    # the step has as many cascade windows as nolb windows
+    rate = 2.0 / (1.0 / rate_c + 1.0 / rate_n)
+    return {"value": rate, "unit": "windows/s", "cores": nt, "kind": "oracle",
+            "sample": (f"oracle FP64 C search, query seed 1: w=103 cascade over the first {nc} windows "
+                       f"({rate_c:.3g} windows/s) and w=1024 nolb over the first {nn} windows "
+                       f"({rate_n:.3g} windows/s), combined for the step's equal mix"),
+            "seconds": round(t2 - t0, 2)}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    for _ in range(args.warmup):
+        cpu_baseline()
+    vals, secs = [], []
+    for _ in range(args.steps):
+        cb = cpu_baseline()
+        vals.append(cb["value"])
+        secs.append(cb["seconds"])
+    v = statistics.mean(vals)
+    cb["value"] = v
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "windows/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(secs),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": workload_desc(args.n), "sample": cb["sample"]},
+            "cpu_baseline": cb,
+            "e2e": {"value": v, "unit": "windows/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--n", type=int, default=N_DEFAULT, help="reference length (default 2e7)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+
+    import torch
+    import torch.distributed as dist
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    import __graft_entry__
+    if rank == 0:
+        __graft_entry__.build()
+    barrier()
+    from paper_2010_05371_gb300 import api, synth
+
+    n = args.n
+    nw = n - M + 1
+    R_np = synth.random_walk(n, 0).astype(np.float32)
+    Qs_np = [synth.random_walk(M, s).astype(np.float32) for s in QUERY_SEEDS]
+    R = torch.from_numpy(R_np).to(dev)
+    Qs = [torch.from_numpy(q).to(dev) for q in Qs_np]
+    stream = torch.cuda.current_stream(dev)
+
+    def step(Rd, Qd):
+        out = []
+        for (w, nolb) in SEARCHES:
+            for q, seed in zip(Qd, QUERY_SEEDS):
+                idx, dist_, cnt = api.subseq_search(q, Rd, w, 1, no_lb=nolb, return_counters=True,
+                                                    stream=stream)
+                out.append((seed, w, nolb, idx, dist_, cnt))
+        return out
+
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > 129 MB L2
+
+    for _ in range(args.warmup):
+        step(R, Qs)
+    torch.cuda.synchronize()
+
+    gpu_uuid = str(torch.cuda.get_device_properties(dev).uuid)
+    gpu_id = gpu_uuid if gpu_uuid.startswith("GPU-") else f"GPU-{gpu_uuid}"
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    step_ms = []
+    results = None
+    main_ns = wider_ns = cells = launches = 0
+    with ClockSampler(gpu_id) as clocks:
+        barrier()
+        torch.cuda.synchronize()
+        t_wall0 = time.perf_counter()
+        for _ in range(args.steps):
+            flush.zero_()          # L2 flushed between steps (outside the timed events)
+            ev0.record(stream)
+            results = step(R, Qs)
+            ev1.record(stream)
+            torch.cuda.synchronize()
+            step_ms.append(ev0.elapsed_time(ev1))
+            for r in results:
+                c = r[5]
+                main_ns += c["ns_main"]
+                wider_ns += c["ns_wider"]
+                cells += c["cells"]
+                launches += c["launches"]
+        torch.cuda.synchronize()
+        barrier()
+        t_wall = time.perf_counter() - t_wall0
+    ms = sum(step_ms) / len(step_ms)
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * len(SEARCHES) * len(QUERY_SEEDS) * nw / (ms / 1e3)
+
+    # ---- end to end: inputs from pinned host memory, results read back ----
+    R_pin = torch.from_numpy(R_np).pin_memory()
+    Q_pin = [torch.from_numpy(q).pin_memory() for q in Qs_np]
+    R2 = torch.empty_like(R)
+    Q2 = [torch.empty_like(q) for q in Qs]
+    e2e_ms = []
+    for it in range(args.steps + 1):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        R2.copy_(R_pin, non_blocking=True)
+        for qd, qh in zip(Q2, Q_pin):
+            qd.copy_(qh, non_blocking=True)
+        res = step(R2, Q2)
+        host = [(int(r[3].cpu()[0]), float(r[4].cpu()[0])) for r in res]  # D2H of every result
+        torch.cuda.synchronize()
+        if it > 0:  # first iteration warms the pinned path
+            e2e_ms.append((time.perf_counter() - t0) * 1e3)
+    e2e = {"value": world * len(SEARCHES) * len(QUERY_SEEDS) * nw / (statistics.mean(e2e_ms) / 1e3),
+           "unit": "windows/s", "h2d_bytes_per_step": 4 * n + 4 * M * len(QUERY_SEEDS),
+           "d2h_bytes_per_step": 16 * len(res), "ms_per_step": statistics.mean(e2e_ms)}
+
+    # ---- roofline of the dominant kernel (search kernel, first level) ----
+    nsearch = args.steps * len(results)
+    props = torch.cuda.get_device_properties(dev)
+    sm_max_mhz = 2070.0
+    clk = clocks.summary()
+    if clk.get("sm_max_mhz"):
+        sm_max_mhz = clk["sm_max_mhz"]
+    peak_tops = props.multi_processor_count * FP32_LANES_PER_SM * sm_max_mhz * 1e6 / 1e12
+    golden = load_golden(n)
+    alg_cells = None
+    if golden:
+        alg_cells = args.steps * sum(golden[(r[0], r[1], not r[2])]["audit_counters"]["cells"]
+                                     for r in results)
+    kern_s = main_ns / 1e9
+    roof = None
+    if kern_s > 0:
+        used_cells = alg_cells if alg_cells is not None else cells
+        achieved = used_cells * OPS_PER_CELL / kern_s / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak_tops, "unit": "Tops/s",
+                "frac": achieved / peak_tops, "traffic": None,
+                "kernel": "search_kernel (LB cascade + EAPrunedDTW wavefront), first level",
+                "kernel_ms_per_launch": main_ns / 1e6 / nsearch,
+                "work": ("algorithmic cells (oracle audit-mode EAPrunedDTW count at ub = NN distance)"
+                         if alg_cells is not None else "executed cells (no oracle count available)"),
+                "ops_per_cell": OPS_PER_CELL,
+                "peak_basis": (f"{props.multi_processor_count} SMs x {FP32_LANES_PER_SM} FP32 lanes x "
+                               f"{sm_max_mhz:.0f} MHz (derived, not measured)")}
+
+    # parity of this run's answers against the oracle's full-size results
+    parity = None
+    if golden:
+        ok = 0
+        for r in results:
+            g = golden[(r[0], r[1], not r[2])]
+            d = float(r[4].cpu()[0])
+            if int(r[3].cpu()[0]) == g["nn_index"] or abs(d - g["nn_dist"]) <= 1e-4 * g["nn_dist"]:
+                if abs(d - g["nn_dist"]) <= 1e-4 * max(g["nn_dist"], 1e-6 * M):
+                    ok += 1
+        parity = f"{ok}/{len(results)} searches match the oracle's nearest neighbour"
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline()
+
+    if rank == 0:
+        per_mode = {}
+        for r in results:
+            key = f"w={r[1]}{' nolb' if r[2] else ' cascade'}"
+            per_mode.setdefault(key, []).append(r[5]["ns_total"] / 1e6)
+        line = {
+            "metric": METRIC, "value": value, "unit": "windows/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": workload_desc(n), "n": n, "m": M, "queries": len(QUERY_SEEDS),
+                       "w": [w for w, _ in SEARCHES], "k": 1,
+                       "l2": "flushed between steps (256 MiB write outside the timed events)",
+                       "parallelism": f"{world} independent replica(s)"},
+            "dtw_cells_per_s": world * cells / args.steps / (ms / 1e3),
+            "algorithmic_cells_per_s": (world * alg_cells / args.steps / (ms / 1e3)) if alg_cells else None,
+            "queries_per_s": world * len(results) / (ms / 1e3),
+            "search_ms": {k: round(statistics.mean(v), 3) for k, v in per_mode.items()},
+            "roofline": roof,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": launches,
+            "clocks": clk,
+            "parity": parity,
+            "wall_s": round(t_wall, 3),
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

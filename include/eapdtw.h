@@ -64,6 +64,14 @@ extern "C" {
 #define EAPDTW_CNT_LB_RECHECK 7     /* LB re-tested against a tighter ub before DTW and skipped */
 #define EAPDTW_CNT_OVERFLOW 8       /* candidates re-run with a wider tile */
 #define EAPDTW_CNT_STEPS 9          /* warp wavefront steps executed */
+/* Device time of the phases of the search, in ns, measured with CUDA events on
+ * the call's stream: */
+#define EAPDTW_CNT_NS_MAIN 10       /* the main search kernel (LB cascade + EAPrunedDTW) */
+#define EAPDTW_CNT_NS_WIDER 11      /* re-runs of overflowed windows with wider tiles */
+#define EAPDTW_CNT_NS_PREP 12       /* window statistics, query preparation, envelope */
+#define EAPDTW_CNT_NS_SEED 13       /* sampled upper-bound seed */
+#define EAPDTW_CNT_NS_TOTAL 14      /* whole call, first to last kernel */
+#define EAPDTW_CNT_LAUNCHES 15      /* kernels launched by the call */
 #define EAPDTW_NCOUNTERS 16
 
 /* eapdtw_strerror: static description of a return code (never NULL). */

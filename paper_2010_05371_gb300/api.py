@@ -23,7 +23,8 @@ _HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__)
 
 NCOUNTERS = 16
 COUNTER_NAMES = ("windows", "kim_pruned", "eq_pruned", "ec_pruned", "dtw_abandoned",
-                 "dtw_completed", "cells", "lb_recheck", "overflow", "steps")
+                 "dtw_completed", "cells", "lb_recheck", "overflow", "steps", "ns_main",
+                 "ns_wider", "ns_prep", "ns_seed", "ns_total", "launches")
 
 
 class SearchOpts(C.Structure):

@@ -20,7 +20,10 @@ PKG = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
-BUILD = os.path.join(PKG, "_build")
+# Developer knobs for tuning experiments: an alternative build directory and
+# extra nvcc flags (e.g. -D overrides of compile-time parameters).
+BUILD = os.environ.get("EAPDTW_BUILD_DIR") or os.path.join(PKG, "_build")
+EXTRA_FLAGS = os.environ.get("EAPDTW_NVCC_FLAGS", "").split()
 LIB = os.path.join(BUILD, "libeapdtw.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
@@ -55,7 +58,7 @@ def build(force: bool = False, verbose_ptxas: bool = False, jobs: int | None = N
     nvcc = _nvcc()
     os.makedirs(BUILD, exist_ok=True)
     common = [nvcc, *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
-              "-I", INCLUDE, "-I", CSRC, "--expt-relaxed-constexpr"]
+              "-I", INCLUDE, "-I", CSRC, "--expt-relaxed-constexpr", *EXTRA_FLAGS]
     if verbose_ptxas:
         common += ["-Xptxas", "-v"]
     objs = []

@@ -90,6 +90,8 @@ struct Scratch {
     int64_t cap_dq = 0, cap_dr = 0;
     int64_t* dIdx = nullptr;
     double* dDist = nullptr;
+    // phase timing of the last search (CUDA events on the caller's stream)
+    cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
 
     unsigned long long* slots() { return reinterpret_cast<unsigned long long*>(state); }
     unsigned long long* counters() { return reinterpret_cast<unsigned long long*>(state + 512); }
@@ -147,6 +149,13 @@ Scratch* scratch_for_current_device(int* dev_out) {
             cudaGetLastError();
             delete s;
             return nullptr;
+        }
+        for (auto& e : s->ev) {
+            if (cudaEventCreate(&e) != cudaSuccess) {
+                cudaGetLastError();
+                delete s;
+                return nullptr;
+            }
         }
         g_scratch[dev] = s;
     }
@@ -208,11 +217,18 @@ int32_t search_impl(Scratch& S, const float* Q, int64_t lQ, const float* R, int6
     }
 
     int* ints = S.ints();
+    int launches = 0;
+    CK(cudaEventRecord(S.ev[0], st));
     CK(launch_init_state(S.slots(), k, S.ub_seed(), S.counters(), ints, kNumInts, st));
     CK(cudaMemsetAsync(S.seed_counters(), 0, 128, st));
     CK(launch_ref_prefix(R, n, S.P1, S.P2, S.T1, S.T2, S.A, ints + kBad, st));
     CK(launch_query_prep(Q, m, wi, S.zq, S.uq, S.lq, S.zqo, S.ord, ints + kBad, st));
-    if (use_lb) CK(launch_envelope(R, n, wi < m - 1 ? wi : m - 1, S.UR, S.LR, st));
+    launches += 3;
+    if (use_lb) {
+        CK(launch_envelope(R, n, wi < m - 1 ? wi : m - 1, S.UR, S.LR, st));
+        ++launches;
+    }
+    CK(cudaEventRecord(S.ev[1], st));
 
     SearchArgs a{};
     a.ref = RefView{R, n, S.P1, S.P2, S.T1, S.T2, S.A};
@@ -242,8 +258,11 @@ int32_t search_impl(Scratch& S, const float* Q, int64_t lQ, const float* R, int6
         sa.ovf_cap = 0;
         sa.counters = S.seed_counters();  // kept apart from the search's own counts
         const int K = plan.K[plan.nlev - 1];
-        CK(launch_search(K, plan.band[plan.nlev - 1], sa, search_blocks(K, plan.band[plan.nlev - 1], m) / 4 + 1, st));
+        const int bd = plan.band[plan.nlev - 1];
+        CK(launch_search(K, bd, false, sa, search_blocks(K, bd, false, m) / 4 + 1, st));
+        launches += 3;
     }
+    CK(cudaEventRecord(S.ev[2], st));
     for (int lev = 0; lev < plan.nlev; ++lev) {
         SearchArgs la = a;
         la.work_counter = ints + kWork0 + lev;
@@ -255,15 +274,35 @@ int32_t search_impl(Scratch& S, const float* Q, int64_t lQ, const float* R, int6
             la.ovf_in_count = ints + kOvf0 + lev - 1;
             la.ovf_in_cap = S.cap_ovf;
         }
-        CK(launch_search(plan.K[lev], plan.band[lev], la, search_blocks(plan.K[lev], plan.band[lev], m), st));
+        const bool lb = use_lb && lev == 0;
+        CK(launch_search(plan.K[lev], plan.band[lev], lb, la, search_blocks(plan.K[lev], plan.band[lev], lb, m), st));
+        ++launches;
+        if (lev == 0) CK(cudaEventRecord(S.ev[3], st));
     }
+    CK(cudaEventRecord(S.ev[4], st));
     CK(launch_finalize(S.slots(), k, out_idx, out_dist, st));
+    ++launches;
+    CK(cudaEventRecord(S.ev[5], st));
     CK(cudaMemcpyAsync(S.host_state, S.state + 512, 384, cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     const unsigned long long* hc = reinterpret_cast<const unsigned long long*>(S.host_state);
     const int* hi = reinterpret_cast<const int*>(S.host_state + 256);
     if (opts && opts->counters) {
         for (int c = 0; c < EAPDTW_NCOUNTERS; ++c) opts->counters[c] = static_cast<int64_t>(hc[c]);
+        auto ns = [&](int a, int b) -> int64_t {
+            float ms = 0.0f;
+            if (cudaEventElapsedTime(&ms, S.ev[a], S.ev[b]) != cudaSuccess) {
+                cudaGetLastError();
+                return -1;
+            }
+            return static_cast<int64_t>(ms * 1.0e6);
+        };
+        opts->counters[EAPDTW_CNT_NS_MAIN] = ns(2, 3);
+        opts->counters[EAPDTW_CNT_NS_WIDER] = ns(3, 4);
+        opts->counters[EAPDTW_CNT_NS_PREP] = ns(0, 1);
+        opts->counters[EAPDTW_CNT_NS_SEED] = ns(1, 2);
+        opts->counters[EAPDTW_CNT_NS_TOTAL] = ns(0, 5);
+        opts->counters[EAPDTW_CNT_LAUNCHES] = launches;
     }
     if (hi[kBad]) return EAPDTW_ERR_NAN_INPUT;
     for (int lev = 0; lev + 1 < plan.nlev; ++lev)
@@ -448,30 +487,30 @@ int32_t eapdtw_release_scratch(void) {
 
 namespace eapdtw {
 
-cudaError_t launch_search_k4(int band, const SearchArgs& args, int blocks, cudaStream_t s);
-cudaError_t launch_search_k8(int band, const SearchArgs& args, int blocks, cudaStream_t s);
-cudaError_t launch_search_k16(int band, const SearchArgs& args, int blocks, cudaStream_t s);
-cudaError_t launch_search_k32(int band, const SearchArgs& args, int blocks, cudaStream_t s);
-int search_blocks_k4(int band, int m);
-int search_blocks_k8(int band, int m);
-int search_blocks_k16(int band, int m);
-int search_blocks_k32(int band, int m);
+cudaError_t launch_search_k4(int band, bool lb, const SearchArgs& args, int blocks, cudaStream_t s);
+cudaError_t launch_search_k8(int band, bool lb, const SearchArgs& args, int blocks, cudaStream_t s);
+cudaError_t launch_search_k16(int band, bool lb, const SearchArgs& args, int blocks, cudaStream_t s);
+cudaError_t launch_search_k32(int band, bool lb, const SearchArgs& args, int blocks, cudaStream_t s);
+int search_blocks_k4(int band, bool lb, int m);
+int search_blocks_k8(int band, bool lb, int m);
+int search_blocks_k16(int band, bool lb, int m);
+int search_blocks_k32(int band, bool lb, int m);
 
-cudaError_t launch_search(int K, int band, const SearchArgs& args, int blocks, cudaStream_t s) {
+cudaError_t launch_search(int K, int band, bool lb, const SearchArgs& args, int blocks, cudaStream_t s) {
     switch (K) {
-        case 4: return launch_search_k4(band, args, blocks, s);
-        case 8: return launch_search_k8(band, args, blocks, s);
-        case 16: return launch_search_k16(band, args, blocks, s);
-        default: return launch_search_k32(band, args, blocks, s);
+        case 4: return launch_search_k4(band, lb, args, blocks, s);
+        case 8: return launch_search_k8(band, lb, args, blocks, s);
+        case 16: return launch_search_k16(band, lb, args, blocks, s);
+        default: return launch_search_k32(band, lb, args, blocks, s);
     }
 }
 
-int search_blocks(int K, int band, int m) {
+int search_blocks(int K, int band, bool lb, int m) {
     switch (K) {
-        case 4: return search_blocks_k4(band, m);
-        case 8: return search_blocks_k8(band, m);
-        case 16: return search_blocks_k16(band, m);
-        default: return search_blocks_k32(band, m);
+        case 4: return search_blocks_k4(band, lb, m);
+        case 8: return search_blocks_k8(band, lb, m);
+        case 16: return search_blocks_k16(band, lb, m);
+        default: return search_blocks_k32(band, lb, m);
     }
 }
 

@@ -104,44 +104,117 @@ __device__ __forceinline__ DtwOut dtw_warp(const float* __restrict__ rows, float
     DtwOut out{INF, 0, 0, 0};
     int busy = 0;
 
-    for (int t = 1;; ++t) {
+    // One wavefront step for row r of this lane's block.  f1 is the position,
+    // in the block, of the column just left of the band (the one just right of
+    // it is f1 + 2w + 2); both are forced to +inf.
+    auto cells = [&](float z, float lin, int f1) {
+        float diag = lprev;
+        float left = lin;
+        int kf = -1, kf2 = -1;
+        if (BAND != 0) {
+            const int f2 = f1 + 2 * w + 2;
+            kf = (static_cast<unsigned>(f1) < static_cast<unsigned>(K)) ? f1 : f2;
+            kf2 = f2;
+        }
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const float top = prv[k];
+            const float d = __fsub_rn(z, zc[k]);
+            float v = __fmaf_rn(d, d, fminf(fminf(top, diag), left));
+            if (BAND == 1) v = (k == kf) ? INF : v;
+            if (BAND == 2) v = (k == kf || k == kf2) ? INF : v;
+            diag = top;
+            left = v;
+            prv[k] = v;
+        }
+        lout = prv[K - 1];
+        omin = fminf(omin, lout);
+    };
+    auto block_min = [&]() {
+        float bmin = prv[0];
+#pragma unroll
+        for (int k = 1; k < K; ++k) bmin = fminf(bmin, prv[k]);
+        return bmin;
+    };
+    // Border / abandon checks after step t (t a multiple of kCheckEvery):
+    // returns true when the candidate is finished (abandoned or overflowed).
+    auto check = [&](float bmin_b, int t) -> bool {
+        ub = fminf(ub, ub_next);
+        const unsigned dead_b = __ballot_sync(kFull, !(bmin_b <= ub));
+        // Overflow: the last block of the window passed an alive value to a
+        // block outside the window.
+        const bool ovf = __shfl_sync(kFull, omin <= ub, 31) && (B0 + 31 < bm);
+        if (ovf) {
+            out.status = 1;
+            out.steps = t;
+            return true;
+        }
+        // Retire leading blocks: block 0 of the window needs to be dead now;
+        // block j >= 1 also needs block j-1 dead one step earlier (that value
+        // is its diagonal input at the next row).
+        const unsigned cond = dead_b & ((dead_a << 1) | 1u);
+        const int d = (cond == kFull) ? 32 : (__ffs(~cond) - 1);
+        if (d == 32 || (dead_a == kFull && dead_b == kFull)) {
+            out.dist = INF;  // every cell of the frontier is above ub
+            out.steps = t;
+            return true;
+        }
+        ub_next = bsf.load();
+        omin = INF;
+        if (d > 0) {
+            B0 += d;
+            const bool fresh = lane >= 32 - d;
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                const float v = __shfl_down_sync(kFull, prv[k], d);
+                prv[k] = fresh ? INF : v;
+            }
+            const float lp = __shfl_down_sync(kFull, lprev, d);
+            const float lo = __shfl_down_sync(kFull, lout, d);
+            lprev = fresh ? INF : lp;
+            lout = fresh ? INF : lo;
+            load_cols();
+        }
+        return false;
+    };
+
+    int t = 0;  // last completed step
+    for (;;) {
+        // Fast path: the next kCheckEvery steps keep every lane's row inside
+        // [1, nr] and stop short of the final step, so no per-lane range test.
+        if ((t & (kCheckEvery - 1)) == 0 && t + 1 - (B0 + 31) >= 1 && t + kCheckEvery - B0 <= nr &&
+            t + kCheckEvery < t_end) {
+            const int b = B0 + lane;
+            const float* rp = rows + (t - b - 1);  // rp[s] = rows[r - 1], r = t + s - b
+            const int f1base = t - b - w - 1 - b * K - 1;
+            float bmin_a = INF, bmin_b = INF;
+#pragma unroll
+            for (int s = 1; s <= kCheckEvery; ++s) {
+                float lin = __shfl_up_sync(kFull, lout, 1);
+                lin = (lane == 0) ? INF : lin;
+                cells(znorm1(rp[s], a, cw, isd), lin, f1base + s);
+                lprev = lin;
+                if (s == kCheckEvery - 1) bmin_a = block_min();
+                if (s == kCheckEvery) bmin_b = block_min();
+            }
+            busy += kCheckEvery;
+            t += kCheckEvery;
+            dead_a = __ballot_sync(kFull, !(bmin_a <= ub));
+            if (check(bmin_b, t)) break;
+            continue;
+        }
+        // General step with per-lane range tests (pipeline fill and drain).
+        ++t;
         const int b = B0 + lane;
         const int r = t - b;
         float lin = __shfl_up_sync(kFull, lout, 1);
         if (lane == 0) lin = INF;
         const int phase = t & (kCheckEvery - 1);
-        const bool chk = phase == 0 || phase == kCheckEvery - 1;
         float bmin = INF;
         if (r >= 1 && r <= nr) {
-            const float z = znorm1(rows[r - 1], a, cw, isd);
-            float diag = lprev;
-            float left = lin;
-            int kf = -1, kf2 = -1;
-            if (BAND != 0) {
-                const int c0 = b * K + 1;
-                const int f1 = r - w - 1 - c0;   // column just left of the band
-                const int f2 = r + w + 1 - c0;   // column just right of the band
-                kf = (f1 >= 0 && f1 < K) ? f1 : f2;
-                kf2 = f2;
-            }
-#pragma unroll
-            for (int k = 0; k < K; ++k) {
-                const float top = prv[k];
-                const float d = __fsub_rn(z, zc[k]);
-                float v = __fmaf_rn(d, d, fminf(fminf(top, diag), left));
-                if (BAND == 1) v = (k == kf) ? INF : v;
-                if (BAND == 2) v = (k == kf || k == kf2) ? INF : v;
-                diag = top;
-                left = v;
-                prv[k] = v;
-            }
-            lout = prv[K - 1];
-            omin = fminf(omin, lout);
+            cells(znorm1(rows[r - 1], a, cw, isd), lin, r - w - 1 - (b * K + 1));
             ++busy;
-            if (chk) {
-#pragma unroll
-                for (int k = 0; k < K; ++k) bmin = fminf(bmin, prv[k]);
-            }
+            if (phase == 0 || phase == kCheckEvery - 1) bmin = block_min();
         } else if (r < 1) {
             lout = INF;
         }
@@ -165,42 +238,7 @@ __device__ __forceinline__ DtwOut dtw_warp(const float* __restrict__ rows, float
         if (phase == kCheckEvery - 1) {
             dead_a = __ballot_sync(kFull, !(bmin <= ub));
         } else if (phase == 0) {
-            ub = fminf(ub, ub_next);
-            const unsigned dead_b = __ballot_sync(kFull, !(bmin <= ub));
-            // Overflow: the last block of the window passed an alive value to a
-            // block outside the window.
-            const bool ovf = __shfl_sync(kFull, omin <= ub, 31) && (B0 + 31 < bm);
-            if (ovf) {
-                out.status = 1;
-                out.steps = t;
-                break;
-            }
-            // Retire leading blocks: block 0 of the window needs to be dead now;
-            // block j >= 1 also needs block j-1 dead one step earlier (that
-            // value is its diagonal input at the next row).
-            const unsigned cond = dead_b & ((dead_a << 1) | 1u);
-            const int d = (cond == kFull) ? 32 : (__ffs(~cond) - 1);
-            if (d == 32 || (dead_a == kFull && dead_b == kFull)) {
-                out.dist = INF;  // every cell of the frontier is above ub
-                out.steps = t;
-                break;
-            }
-            ub_next = bsf.load();
-            omin = INF;
-            if (d > 0) {
-                B0 += d;
-                const bool fresh = lane >= 32 - d;
-#pragma unroll
-                for (int k = 0; k < K; ++k) {
-                    const float v = __shfl_down_sync(kFull, prv[k], d);
-                    prv[k] = fresh ? INF : v;
-                }
-                const float lp = __shfl_down_sync(kFull, lprev, d);
-                const float lo = __shfl_down_sync(kFull, lout, d);
-                lprev = fresh ? INF : lp;
-                lout = fresh ? INF : lo;
-                load_cols();
-            }
+            if (check(bmin, t)) break;
         }
     }
     // warp totals of busy lane-steps

@@ -24,10 +24,11 @@ cudaError_t launch_seed(const RefView& ref, const float* zq, int m, int64_t nw, 
 cudaError_t launch_finalize(const unsigned long long* slots, int k, int64_t* out_idx,
                             double* out_dist, cudaStream_t s);
 
-// search_kernel<K, BAND> for K in {4, 8, 16, 32} and BAND in {0, 1, 2}; one
-// translation unit per K.  blocks = 0 picks a persistent grid from occupancy.
-cudaError_t launch_search(int K, int band, const SearchArgs& args, int blocks, cudaStream_t s);
-int search_blocks(int K, int band, int m);
+// search_kernel<K, BAND, LB> for K in {4, 8, 16, 32}, BAND in {0, 1, 2} and
+// LB in {false, true}; one translation unit per K.  search_blocks gives the
+// persistent grid (resident blocks per SM x SMs).
+cudaError_t launch_search(int K, int band, bool lb, const SearchArgs& args, int blocks, cudaStream_t s);
+int search_blocks(int K, int band, bool lb, int m);
 
 // eap_dtw single pair: one warp.
 cudaError_t launch_pair(int K, int band, const float* rows, int nr, const float* cols, int nc, int w,

@@ -4,27 +4,24 @@
 
 namespace eapdtw {
 
-template __global__ void search_kernel<32, 0>(const SearchArgs);
-template __global__ void search_kernel<32, 1>(const SearchArgs);
-template __global__ void search_kernel<32, 2>(const SearchArgs);
 
 namespace {
-template <int BAND>
+template <int BAND, bool LB>
 cudaError_t launch_band(const SearchArgs& args, int blocks, cudaStream_t s) {
     const size_t sm = search_smem_bytes(args.q.m);
-    cudaError_t e = cudaFuncSetAttribute(search_kernel<32, BAND>,
+    cudaError_t e = cudaFuncSetAttribute(search_kernel<32, BAND, LB>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(sm));
     if (e != cudaSuccess) return e;
-    search_kernel<32, BAND><<<blocks, search_warps(args.q.m) * 32, sm, s>>>(args);
+    search_kernel<32, BAND, LB><<<blocks, search_warps(args.q.m) * 32, sm, s>>>(args);
     return cudaGetLastError();
 }
-template <int BAND>
+template <int BAND, bool LB>
 int occupancy_blocks(int m) {
     const size_t sm = search_smem_bytes(m);
-    cudaFuncSetAttribute(search_kernel<32, BAND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(search_kernel<32, BAND, LB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          static_cast<int>(sm));
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, search_kernel<32, BAND>,
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, search_kernel<32, BAND, LB>,
                                                       search_warps(m) * 32, sm) != cudaSuccess)
         per_sm = 1;
     int dev = 0, sms = 0;
@@ -34,16 +31,26 @@ int occupancy_blocks(int m) {
 }
 }  // namespace
 
-cudaError_t launch_search_k32(int band, const SearchArgs& args, int blocks, cudaStream_t s) {
-    if (band == 0) return launch_band<0>(args, blocks, s);
-    if (band == 1) return launch_band<1>(args, blocks, s);
-    return launch_band<2>(args, blocks, s);
+cudaError_t launch_search_k32(int band, bool lb, const SearchArgs& args, int blocks, cudaStream_t s) {
+    if (lb) {
+        if (band == 0) return launch_band<0, true>(args, blocks, s);
+        if (band == 1) return launch_band<1, true>(args, blocks, s);
+        return launch_band<2, true>(args, blocks, s);
+    }
+    if (band == 0) return launch_band<0, false>(args, blocks, s);
+    if (band == 1) return launch_band<1, false>(args, blocks, s);
+    return launch_band<2, false>(args, blocks, s);
 }
 
-int search_blocks_k32(int band, int m) {
-    if (band == 0) return occupancy_blocks<0>(m);
-    if (band == 1) return occupancy_blocks<1>(m);
-    return occupancy_blocks<2>(m);
+int search_blocks_k32(int band, bool lb, int m) {
+    if (lb) {
+        if (band == 0) return occupancy_blocks<0, true>(m);
+        if (band == 1) return occupancy_blocks<1, true>(m);
+        return occupancy_blocks<2, true>(m);
+    }
+    if (band == 0) return occupancy_blocks<0, false>(m);
+    if (band == 1) return occupancy_blocks<1, false>(m);
+    return occupancy_blocks<2, false>(m);
 }
 
 }  // namespace eapdtw

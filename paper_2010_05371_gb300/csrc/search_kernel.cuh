@@ -64,8 +64,19 @@ __host__ inline size_t search_smem_bytes(int m) {
     return sizeof(float) * (5 * static_cast<size_t>(mp) + search_warps(m) * static_cast<size_t>(tile_floats(m)));
 }
 
-template <int K, int BAND>
-__global__ void __launch_bounds__(kWarpsPerBlock * 32)
+// Resident blocks per SM the register allocation is sized for (registers per
+// thread <= 65536 / (256 * blocks)): the DP row takes 2K registers per lane.
+#ifndef EAPDTW_MINB16
+#define EAPDTW_MINB16 3
+#endif
+__host__ __device__ constexpr int search_min_blocks(int K) {
+    return K <= 8 ? 4 : (K <= 16 ? EAPDTW_MINB16 : 2);
+}
+
+// LB: compile the lower-bound cascade in (true) or out (false, the "nolb"
+// variant and the list-mode re-runs); leaving it out frees registers.
+template <int K, int BAND, bool LB>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32, search_min_blocks(K))
 search_kernel(const SearchArgs A) {
     extern __shared__ __align__(16) float smem[];
     const int m = A.q.m;
@@ -79,6 +90,9 @@ search_kernel(const SearchArgs A) {
     const int lane = threadIdx.x & 31;
     float* s_r = reinterpret_cast<float*>(s_ord + mp) + warp * tile_floats(m);
 
+    // block-level counters (shared 64-bit atomics), flushed to global at the end
+    __shared__ unsigned long long s_cnt[10];
+    if (threadIdx.x < 10) s_cnt[threadIdx.x] = 0;
     for (int j = threadIdx.x; j < mp; j += blockDim.x) {
         s_zq[j] = j < m ? A.q.zq[j] : f_nan();
         s_uq[j] = A.q.uq_o[j];
@@ -89,16 +103,13 @@ search_kernel(const SearchArgs A) {
     __syncthreads();
 
     const bool list_mode = A.ovf_in != nullptr;
-    const int64_t n = A.ref.n;
     int64_t nitems = (A.nw + 31) / 32;
     if (list_mode) {
         const int c = *A.ovf_in_count;
         nitems = c < A.ovf_in_cap ? c : A.ovf_in_cap;
     }
     const bool r_aligned = (reinterpret_cast<uintptr_t>(A.ref.R) & 15) == 0;
-    // per-lane counters (summed over the warp at the end)
-    unsigned long long c_win = 0, c_kim = 0, c_eq = 0, c_ec = 0;
-    unsigned long long c_ab = 0, c_done = 0, c_cells = 0, c_re = 0, c_ovf = 0, c_steps = 0;
+    auto count = [&](int c, unsigned long long v) { if (v) atomicAdd(s_cnt + c, v); };
 
     for (;;) {
         int item = 0;
@@ -135,8 +146,8 @@ search_kernel(const SearchArgs A) {
         if (valid) window_coeffs(A.ref, i, m, s_r + my, a, cw, isd);
         float lb = 0.0f;
         bool alive = valid && (!list_mode || lane == 0);
-        if (!list_mode && lane < nlanes) c_win++;
-        if (A.use_lb && alive && !list_mode) {
+        int why = 0;  // 1, 2, 3: pruned by LB_Kim, LB_Keogh EQ, LB_Keogh EC
+        if (LB && A.use_lb && alive && !list_mode) {
             const float ub = A.bsf.load() * A.lb_scale;
             const float* x = s_r + my;
             const float z0 = znorm1(x[0], a, cw, isd);
@@ -149,7 +160,7 @@ search_kernel(const SearchArgs A) {
             lb = kim;
             if (kim > ub) {
                 alive = false;
-                c_kim++;
+                why = 1;
             } else {
                 // LB_Keogh EQ: the normalised window against the query envelope.
                 float s = 0.0f;
@@ -166,7 +177,7 @@ search_kernel(const SearchArgs A) {
                 lb = fmaxf(lb, s);
                 if (s > ub) {
                     alive = false;
-                    c_eq++;
+                    why = 2;
                 } else {
                     // LB_Keogh EC: the query against the window's envelope.
                     float s2 = 0.0f;
@@ -187,9 +198,21 @@ search_kernel(const SearchArgs A) {
                     lb = fmaxf(lb, s2);
                     if (s2 > ub) {
                         alive = false;
-                        c_ec++;
+                        why = 3;
                     }
                 }
+            }
+        }
+
+        if (!list_mode) {
+            const unsigned b1 = __ballot_sync(kFull, why == 1);
+            const unsigned b2 = __ballot_sync(kFull, why == 2);
+            const unsigned b3 = __ballot_sync(kFull, why == 3);
+            if (lane == 0) {
+                count(kCntWindows, nlanes);
+                count(kCntKim, __popc(b1));
+                count(kCntEq, __popc(b2));
+                count(kCntEc, __popc(b3));
             }
         }
 
@@ -205,18 +228,18 @@ search_kernel(const SearchArgs A) {
             const int off = list_mode ? 0 : src;
             const int64_t iw = i0 + off;
             float ub = A.bsf.load();
-            if (A.use_lb && !list_mode && lb_s > ub * A.lb_scale) {
-                if (lane == 0) c_re++;
+            if (LB && A.use_lb && !list_mode && lb_s > ub * A.lb_scale) {
+                if (lane == 0) count(kCntRecheck, 1);
                 continue;
             }
             const DtwOut o = dtw_warp<K, BAND>(s_r + off, a_s, cw_s, isd_s, s_zq, m, m, A.w, A.bsf, ub);
             if (lane == 0) {
-                c_steps += static_cast<unsigned long long>(o.steps);
-                c_cells += static_cast<unsigned long long>(o.busy) * K;
+                count(kCntSteps, static_cast<unsigned long long>(o.steps));
+                count(kCntCells, static_cast<unsigned long long>(o.busy) * K);
             }
             if (o.status != 0) {
                 if (lane == 0) {
-                    c_ovf++;
+                    count(kCntOverflow, 1);
                     const int slot = atomicAdd(A.ovf_out_count, 1);
                     if (slot < A.ovf_cap) A.ovf_out[slot] = static_cast<int>(iw);
                 }
@@ -226,24 +249,17 @@ search_kernel(const SearchArgs A) {
             if (o.dist <= ub) {
                 if (lane == 0) {
                     A.bsf.insert(o.dist, static_cast<uint32_t>(iw));
-                    c_done++;
+                    count(kCntCompleted, 1);
                 }
             } else if (lane == 0) {
-                c_ab++;
+                count(kCntAbandoned, 1);
             }
         }
         __syncwarp();
     }
 
-    // warp-sum of the per-lane counters, one atomic per counter per warp
-    unsigned long long v[10] = {c_win, c_kim, c_eq, c_ec, c_ab, c_done, c_cells, c_re, c_ovf, c_steps};
-#pragma unroll
-    for (int c = 0; c < 10; ++c) {
-        unsigned long long x = v[c];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(kFull, x, o);
-        if (lane == 0 && x) atomicAdd(A.counters + c, x);
-    }
+    __syncthreads();
+    if (threadIdx.x < 10 && s_cnt[threadIdx.x]) atomicAdd(A.counters + threadIdx.x, s_cnt[threadIdx.x]);
 }
 
 }  // namespace eapdtw
