@@ -156,6 +156,36 @@ int32_t subseq_search_host(const float* Q, int64_t lQ, const float* R, int64_t l
 /* eapdtw_release_scratch - free the cached scratch memory of the current device. */
 int32_t eapdtw_release_scratch(void);
 
+/*
+ * subseq_search_noalloc - subseq_search for callers that cannot allocate memory.
+ *
+ * The paper has no counterpart: this entry point exists for callers that must
+ * not call cudaMalloc, for example code running inside a memory pool or an
+ * allocator they do not own, or under a policy that forbids device allocation
+ * after start-up.  It computes exactly what subseq_search computes, with the
+ * same arguments and results, but it allocates nothing, on the device or the
+ * host.  Its scratch memory (window statistics, envelopes, query staging,
+ * best-so-far state, work lists) is one fixed array in the library's device
+ * memory, EAPDTW_NOALLOC_SCRATCH_BYTES long, which every GPU that loads the
+ * library keeps until the process exits.
+ *
+ *   Limits: lR <= EAPDTW_NOALLOC_MAX_N, lQ <= EAPDTW_MAX_QUERY,
+ *           k <= EAPDTW_MAX_K.  Larger sizes return EAPDTW_ERR_UNSUPPORTED
+ *           and launch nothing.
+ *   Pointers, stream and blocking behaviour are those of subseq_search.
+ *   The first call on a device looks up the array's device address on that
+ *   device; make that first call before any stream capture.
+ *   All calls share the one array, and each call leaves its contents behind;
+ *   the call clears what must start from zero itself.  Calls are serialised
+ *   on the host, and each returns only after its work is done; two calls that
+ *   overlapped on the GPU (for example from a launch issued around this API)
+ *   would race on the array.
+ */
+#define EAPDTW_NOALLOC_MAX_N (1 << 20)
+#define EAPDTW_NOALLOC_SCRATCH_BYTES (32 * (int64_t)EAPDTW_NOALLOC_MAX_N + (1 << 20))
+int32_t subseq_search_noalloc(const float* Q, int64_t lQ, const float* R, int64_t lR, int64_t w,
+                              int32_t k, int64_t* out_idx, double* out_dist, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -74,6 +74,8 @@ def lib():
         L.subseq_search_host.argtypes = [vp, i64, vp, i64, i64, i32, C.POINTER(SearchOpts), vp, vp]
         L.eapdtw_release_scratch.restype = i32
         L.eapdtw_release_scratch.argtypes = []
+        L.subseq_search_noalloc.restype = i32
+        L.subseq_search_noalloc.argtypes = [vp, i64, vp, i64, i64, i32, vp, vp, vp]
         _lib = L
     return _lib
 
@@ -193,6 +195,19 @@ def subseq_search_host(Q, R, w: int, k: int = 1, *, no_lb: bool = False, tile: i
     _check(rc, "subseq_search_host")
     if return_counters:
         return idx, dist, dict(zip(COUNTER_NAMES, (int(c) for c in cnt)))
+    return idx, dist
+
+
+def subseq_search_noalloc(Q, R, w: int, idx, dist, stream=None):
+    """subseq_search into caller-provided idx (int64[k]) and dist (float64[k])
+    CUDA tensors, through the entry point that allocates nothing (for callers
+    that cannot allocate device memory).  k = idx.numel().  Blocking."""
+    Q, R = _dev_f32(Q, "Q"), _dev_f32(R, "R")
+    k = idx.numel()
+    rc = lib().subseq_search_noalloc(C.c_void_p(Q.data_ptr()), Q.numel(), C.c_void_p(R.data_ptr()),
+                                     R.numel(), int(w), int(k), C.c_void_p(idx.data_ptr()),
+                                     C.c_void_p(dist.data_ptr()), _stream_ptr(stream))
+    _check(rc, "subseq_search_noalloc")
     return idx, dist
 
 
