@@ -41,6 +41,9 @@ GOLDEN = os.path.join(ROOT, "tests", "golden", "bench_large_oracle.json")
 # fma(d, d, .) -- four FP32-pipe instructions.
 OPS_PER_CELL = 4
 FP32_LANES_PER_SM = 128
+# DRAM bytes (read + write) of the search kernel per search, from ncu; None until
+# captured for the current kernel (see profiles/).
+TRAFFIC_BYTES_PER_SEARCH = None
 # CPU baseline sample (oracle): windows of the cascade (w=103) and nolb (w=1024) searches
 CPU_SAMPLE = {"cascade_windows": 2_000_000, "nolb_windows": 200_000, "query_seed": 1}
 
@@ -186,7 +189,14 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--n", type=int, default=N_DEFAULT, help="reference length (default 2e7)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--mode", default="all", choices=["all", "cascade", "nolb"],
+                    help="searches per step (profiling aid; the benchmark is 'all')")
     args = ap.parse_args()
+    global SEARCHES
+    if args.mode == "cascade":
+        SEARCHES = [SEARCHES[0]]
+    elif args.mode == "nolb":
+        SEARCHES = [SEARCHES[1]]
     if args.impl == "reference":
         run_reference(args)
         return
@@ -302,20 +312,25 @@ def main():
     if golden:
         alg_cells = args.steps * sum(golden[(r[0], r[1], not r[2])]["audit_counters"]["cells"]
                                      for r in results)
-    kern_s = main_ns / 1e9
+    # every search_kernel launch of the search except the seed pass: the first
+    # level (all windows) and the re-runs of overflowed windows with wider tiles
+    kern_s = (main_ns + wider_ns) / 1e9
     roof = None
     if kern_s > 0:
         used_cells = alg_cells if alg_cells is not None else cells
         achieved = used_cells * OPS_PER_CELL / kern_s / 1e12
+        executed = cells * OPS_PER_CELL / kern_s / 1e12
         roof = {"bound": "alu", "achieved": achieved, "peak": peak_tops, "unit": "Tops/s",
-                "frac": achieved / peak_tops, "traffic": None,
-                "kernel": "search_kernel (LB cascade + EAPrunedDTW wavefront), first level",
-                "kernel_ms_per_launch": main_ns / 1e6 / nsearch,
+                "frac": achieved / peak_tops, "traffic": TRAFFIC_BYTES_PER_SEARCH,
+                "kernel": "search_kernel (LB cascade + EAPrunedDTW wavefront), all levels of a search",
+                "kernel_ms_per_search": (main_ns + wider_ns) / 1e6 / nsearch,
                 "work": ("algorithmic cells (oracle audit-mode EAPrunedDTW count at ub = NN distance)"
                          if alg_cells is not None else "executed cells (no oracle count available)"),
+                "executed_cells_achieved": executed, "executed_cells_frac": executed / peak_tops,
+                "executed_over_algorithmic": (cells / alg_cells) if alg_cells else None,
                 "ops_per_cell": OPS_PER_CELL,
                 "peak_basis": (f"{props.multi_processor_count} SMs x {FP32_LANES_PER_SM} FP32 lanes x "
-                               f"{sm_max_mhz:.0f} MHz (derived, not measured)")}
+                               f"{sm_max_mhz:.0f} MHz (derived from unit counts and clock, not measured)")}
 
     # parity of this run's answers against the oracle's full-size results
     parity = None

@@ -46,10 +46,15 @@ Plan plan_levels(int64_t nr, int64_t nc, int64_t w, int tile_hint) {
             if (32 * K >= nc) { k0 = K; break; }
     }
     Plan p;
+    int covered = 0;  // columns of the widest window of the previous level
     for (int K = k0; K <= 32; K *= 2) {
+        const int band = unconstrained ? 0 : (K <= 2 * w + 2 ? 1 : 2);
+        const int cols = 32 * K * dtw_windows(K, band);
+        if (cols <= covered) continue;
         p.K[p.nlev] = K;
-        p.band[p.nlev] = unconstrained ? 0 : (K <= 2 * w + 2 ? 1 : 2);
+        p.band[p.nlev] = band;
         ++p.nlev;
+        covered = cols;
     }
     return p;
 }

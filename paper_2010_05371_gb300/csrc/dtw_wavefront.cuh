@@ -22,9 +22,14 @@
 //  * Right border (pruning_point, Section 4).  Cells right of the last alive
 //    cell only receive dead inputs from above, so they are dead unless the
 //    left chain keeps them alive; no bookkeeping is needed: they are computed
-//    as dead values inside the window.  A live chain reaching past the
-//    window's last block is an overflow: the caller re-runs the candidate
-//    with a wider block (larger K).
+//    as dead values inside the window.  The window is elastic: up to J
+//    windows of 32 blocks follow one another (lane l also owns block
+//    B0 + 32j + l of window j); window j+1 is switched on when an alive cell
+//    comes within 9 blocks of the end of window j (the live region grows by
+//    at most one block per step, and the checks come every 8 steps), and off
+//    again when it and the end of window j are dead.  A live chain reaching
+//    past the last of the J windows is an overflow: the caller re-runs the
+//    candidate with wider blocks (larger K).
 //  * Early abandoning (border collision / full discard line).  When every
 //    block of the window is dead at two consecutive steps, every later cell
 //    has dead inputs only: the result is +inf.
@@ -55,60 +60,98 @@ struct DtwOut {
     int busy;       // lane-steps that computed a block (cells = busy * K)
 };
 
+// Windows of 32 blocks a candidate may use.  A second window for narrow blocks
+// of the unconstrained case (EAPDTW_WIDE_WINDOWS=2) executes fewer cells on
+// wide candidates but needs about 120 registers per thread, which halves the
+// resident warps; measured on GB300 it ran about 2x slower, so one window is
+// the default and wide live regions are re-run with wider blocks instead.
+#ifndef EAPDTW_WIDE_WINDOWS
+#define EAPDTW_WIDE_WINDOWS 1
+#endif
+__host__ __device__ constexpr int dtw_windows(int K, int BAND) {
+    return (BAND == 0 && K <= 8) ? EAPDTW_WIDE_WINDOWS : 1;
+}
+
 __device__ __forceinline__ float f_inf() { return __int_as_float(0x7f800000); }
 __device__ __forceinline__ float f_nan() { return __int_as_float(0x7fffffff); }
 
 // Rows r = 1..nr take values znorm1(rows[r-1], a, cw, isd); columns c = 1..nc
-// take cols[c-1] (already normalised; cols must be 16-byte aligned).
+// take cols[c-1] (already normalised).
 // BAND = 0: unconstrained (only valid when w >= max(nr, nc) - 1);
 // BAND = 1: banded with K <= 2w + 2 (at most one forced cell per block and row);
 // BAND = 2: banded, any w (two forced cells may share a block).
+// J: windows of 32 blocks available to the live region.
 // All 32 lanes call it with identical arguments.
-template <int K, int BAND>
+template <int K, int BAND, int J = 1>
 __device__ __forceinline__ DtwOut dtw_warp(const float* __restrict__ rows, float a, float cw,
                                            float isd, const float* __restrict__ cols, int nr,
                                            int nc, int w, const BestSoFar bsf, float ub) {
     static_assert(K % 4 == 0, "K must be a multiple of 4");
+    static_assert(J >= 1 && J <= 4, "1 to 4 windows");
     const int lane = threadIdx.x & 31;
     const float INF = f_inf();
-    float prv[K];
-    float zc[K];
+    float prv[J][K];
+    float zc[J][K];
+    float lout[J];    // each window's last cell of this lane's block, previous step
+    float lprev[J];   // left input of the previous step (diagonal of cell 0)
+    float omin[J];    // min of lout since the last check
+    unsigned dead_a[J];
     int B0 = 0;
+    int jact = 1;     // active windows
 
-    auto load_cols = [&]() {
-        const int cb = (B0 + lane) * K;
+    auto load_cols = [&](int j) {
+        const int cb = (B0 + 32 * j + lane) * K;
         if (cb + K <= nc && (reinterpret_cast<uintptr_t>(cols + cb) & 15) == 0) {
             const float4* p = reinterpret_cast<const float4*>(cols + cb);
 #pragma unroll
             for (int q = 0; q < K / 4; ++q) {
                 const float4 v = p[q];
-                zc[4 * q] = v.x; zc[4 * q + 1] = v.y; zc[4 * q + 2] = v.z; zc[4 * q + 3] = v.w;
+                zc[j][4 * q] = v.x; zc[j][4 * q + 1] = v.y; zc[j][4 * q + 2] = v.z; zc[j][4 * q + 3] = v.w;
             }
         } else {
 #pragma unroll
-            for (int k = 0; k < K; ++k) zc[k] = (cb + k < nc) ? cols[cb + k] : f_nan();
+            for (int k = 0; k < K; ++k) zc[j][k] = (cb + k < nc) ? cols[cb + k] : f_nan();
         }
     };
-    load_cols();
+    auto reset = [&](int j) {
 #pragma unroll
-    for (int k = 0; k < K; ++k) prv[k] = INF;
+        for (int k = 0; k < K; ++k) prv[j][k] = INF;
+        lout[j] = INF;
+        lprev[j] = INF;
+        omin[j] = INF;
+        dead_a[j] = kFull;
+    };
+#pragma unroll
+    for (int j = 0; j < J; ++j) {
+        reset(j);
+        load_cols(j);
+    }
+    if (lane == 0) lprev[0] = 0.0f;   // D(0,0) = 0: diagonal of cell (1,1)
 
-    float lout = INF;                         // my block's last cell, previous step
-    float lprev = (lane == 0) ? 0.0f : INF;   // left input of the previous step; D(0,0) = 0
-    float omin = INF;                         // min of lout since the last check
     float ub_next = ub;
-    unsigned dead_a = 0;
-    const int bm = (nc - 1) / K;              // block of the last column
+    const int bm = (nc - 1) / K;       // block of the last column
     const int km = (nc - 1) - bm * K;
-    const int t_end = nr + bm;                // step computing cell (nr, nc)
+    const int t_end = nr + bm;         // step computing cell (nr, nc)
     DtwOut out{INF, 0, 0, 0};
     int busy = 0;
 
-    // One wavefront step for row r of this lane's block.  f1 is the position,
-    // in the block, of the column just left of the band (the one just right of
-    // it is f1 + 2w + 2); both are forced to +inf.
-    auto cells = [&](float z, float lin, int f1) {
-        float diag = lprev;
+    // Left inputs of every active window, read before any lout changes.
+    auto left_inputs = [&](float* lin) {
+#pragma unroll
+        for (int j = 0; j < J; ++j) {
+            if (j < jact) {
+                const float up = __shfl_up_sync(kFull, lout[j], 1);
+                float from_prev = INF;
+                if (j > 0) from_prev = __shfl_sync(kFull, lout[j - 1], 31);
+                lin[j] = (lane == 0) ? from_prev : up;
+            }
+        }
+    };
+    // One wavefront step of window j for row r of this lane's block.  f1 is
+    // the position, in the block, of the column just left of the band (the one
+    // just right of it is f1 + 2w + 2); both are forced to +inf.
+    auto cells = [&](int j, float z, float lin, int f1) {
+        float diag = lprev[j];
         float left = lin;
         int kf = -1, kf2 = -1;
         if (BAND != 0) {
@@ -118,117 +161,175 @@ __device__ __forceinline__ DtwOut dtw_warp(const float* __restrict__ rows, float
         }
 #pragma unroll
         for (int k = 0; k < K; ++k) {
-            const float top = prv[k];
-            const float d = __fsub_rn(z, zc[k]);
+            const float top = prv[j][k];
+            const float d = __fsub_rn(z, zc[j][k]);
             float v = __fmaf_rn(d, d, fminf(fminf(top, diag), left));
             if (BAND == 1) v = (k == kf) ? INF : v;
             if (BAND == 2) v = (k == kf || k == kf2) ? INF : v;
             diag = top;
             left = v;
-            prv[k] = v;
+            prv[j][k] = v;
         }
-        lout = prv[K - 1];
-        omin = fminf(omin, lout);
+        lout[j] = prv[j][K - 1];
+        lprev[j] = lin;
+        omin[j] = fminf(omin[j], lout[j]);
     };
-    auto block_min = [&]() {
-        float bmin = prv[0];
+    auto block_min = [&](int j) {
+        float bmin = prv[j][0];
 #pragma unroll
-        for (int k = 1; k < K; ++k) bmin = fminf(bmin, prv[k]);
+        for (int k = 1; k < K; ++k) bmin = fminf(bmin, prv[j][k]);
         return bmin;
     };
-    // Border / abandon checks after step t (t a multiple of kCheckEvery):
-    // returns true when the candidate is finished (abandoned or overflowed).
-    auto check = [&](float bmin_b, int t) -> bool {
+    // Border / abandon checks after step t (t a multiple of kCheckEvery);
+    // dead_a holds the dead lanes of the step before.  Returns true when the
+    // candidate is finished (abandoned or overflowed).
+    auto check = [&](const float* bmin_b, int t) -> bool {
         ub = fminf(ub, ub_next);
-        const unsigned dead_b = __ballot_sync(kFull, !(bmin_b <= ub));
-        // Overflow: the last block of the window passed an alive value to a
-        // block outside the window.
-        const bool ovf = __shfl_sync(kFull, omin <= ub, 31) && (B0 + 31 < bm);
-        if (ovf) {
+        unsigned db[J];
+#pragma unroll
+        for (int j = 0; j < J; ++j)
+            db[j] = (j < jact) ? __ballot_sync(kFull, !(bmin_b[j] <= ub)) : kFull;
+        // Overflow: the last active window passed an alive value beyond itself.
+        float om = omin[0];
+#pragma unroll
+        for (int j = 1; j < J; ++j) om = (j == jact - 1) ? omin[j] : om;
+        if (__shfl_sync(kFull, om <= ub, 31) && B0 + 32 * jact - 1 < bm) {
             out.status = 1;
             out.steps = t;
             return true;
         }
-        // Retire leading blocks: block 0 of the window needs to be dead now;
+        // Every active block dead at two consecutive steps: abandon.
+        bool all_dead = true;
+#pragma unroll
+        for (int j = 0; j < J; ++j) all_dead &= (j >= jact) || (dead_a[j] == kFull && db[j] == kFull);
+        // Retire leading blocks of window 0: block 0 needs to be dead now;
         // block j >= 1 also needs block j-1 dead one step earlier (that value
         // is its diagonal input at the next row).
-        const unsigned cond = dead_b & ((dead_a << 1) | 1u);
-        const int d = (cond == kFull) ? 32 : (__ffs(~cond) - 1);
-        if (d == 32 || (dead_a == kFull && dead_b == kFull)) {
-            out.dist = INF;  // every cell of the frontier is above ub
+        const unsigned cond = db[0] & ((dead_a[0] << 1) | 1u);
+        if (all_dead || (jact == 1 && cond == kFull)) {
+            out.dist = INF;
             out.steps = t;
             return true;
         }
-        ub_next = bsf.load();
-        omin = INF;
-        if (d > 0) {
-            B0 += d;
-            const bool fresh = lane >= 32 - d;
+        int d = (cond == kFull) ? 31 : (__ffs(~cond) - 1);
+        // Switch the next window on when an alive cell came within 9 blocks
+        // of the end of the last active one; off when the last one and the
+        // end of the one before are dead.
+        if (J > 1) {
+            constexpr unsigned kNear = 0xff800000u;  // lanes 23..31
+            unsigned near_last = 0, near_prev = 0, dead_last = 0;
 #pragma unroll
-            for (int k = 0; k < K; ++k) {
-                const float v = __shfl_down_sync(kFull, prv[k], d);
-                prv[k] = fresh ? INF : v;
+            for (int j = 0; j < J; ++j) {
+                if (j == jact - 1) {
+                    near_last = ~(dead_a[j] & db[j]) & kNear;
+                    dead_last = (dead_a[j] == kFull && db[j] == kFull) ? 1u : 0u;
+                }
+                if (j == jact - 2) near_prev = ~(dead_a[j] & db[j]) & kNear;
             }
-            const float lp = __shfl_down_sync(kFull, lprev, d);
-            const float lo = __shfl_down_sync(kFull, lout, d);
-            lprev = fresh ? INF : lp;
-            lout = fresh ? INF : lo;
-            load_cols();
+            if (jact < J && near_last) {
+                ++jact;  // its state is +inf (reset when it was switched off)
+            } else if (jact > 1 && dead_last && !near_prev) {
+#pragma unroll
+                for (int j = 1; j < J; ++j)
+                    if (j == jact - 1) reset(j);
+                --jact;
+            }
+        }
+        ub_next = bsf.load();
+#pragma unroll
+        for (int j = 0; j < J; ++j) omin[j] = INF;
+        if (d > 0) {
+            // Slide every active window d blocks right: lane l of window j
+            // takes block B0 + d + 32j + l from lane l + d of window j, or from
+            // lane l + d - 32 of window j + 1 (+inf past the active windows).
+            B0 += d;
+            const int src = (lane + d) & 31;
+            const bool from_next = lane < d;
+#pragma unroll
+            for (int j = 0; j < J; ++j) {
+                if (j < jact) {
+                    const bool nxt_on = j + 1 < jact;
+#pragma unroll
+                    for (int k = 0; k < K; ++k) {
+                        const float nx = (j + 1 < J && nxt_on) ? prv[j + 1 < J ? j + 1 : j][k] : INF;
+                        prv[j][k] = __shfl_sync(kFull, from_next ? nx : prv[j][k], src);
+                    }
+                    const float nlo = (j + 1 < J && nxt_on) ? lout[j + 1 < J ? j + 1 : j] : INF;
+                    const float nlp = (j + 1 < J && nxt_on) ? lprev[j + 1 < J ? j + 1 : j] : INF;
+                    lout[j] = __shfl_sync(kFull, from_next ? nlo : lout[j], src);
+                    lprev[j] = __shfl_sync(kFull, from_next ? nlp : lprev[j], src);
+                }
+                load_cols(j);
+            }
         }
         return false;
     };
 
     int t = 0;  // last completed step
     for (;;) {
-        // Fast path: the next kCheckEvery steps keep every lane's row inside
-        // [1, nr] and stop short of the final step, so no per-lane range test.
-        if ((t & (kCheckEvery - 1)) == 0 && t + 1 - (B0 + 31) >= 1 && t + kCheckEvery - B0 <= nr &&
-            t + kCheckEvery < t_end) {
-            const int b = B0 + lane;
-            const float* rp = rows + (t - b - 1);  // rp[s] = rows[r - 1], r = t + s - b
-            const int f1base = t - b - w - 1 - b * K - 1;
-            float bmin_a = INF, bmin_b = INF;
+        // Fast path: the next kCheckEvery steps keep every active lane's row
+        // inside [1, nr] and stop short of the final step: no per-lane tests.
+        if ((t & (kCheckEvery - 1)) == 0 && t + 1 - (B0 + 32 * jact - 1) >= 1 &&
+            t + kCheckEvery - B0 <= nr && t + kCheckEvery < t_end) {
+            float bmin_a[J], bmin_b[J];
 #pragma unroll
             for (int s = 1; s <= kCheckEvery; ++s) {
-                float lin = __shfl_up_sync(kFull, lout, 1);
-                lin = (lane == 0) ? INF : lin;
-                cells(znorm1(rp[s], a, cw, isd), lin, f1base + s);
-                lprev = lin;
-                if (s == kCheckEvery - 1) bmin_a = block_min();
-                if (s == kCheckEvery) bmin_b = block_min();
+                float lin[J];
+                left_inputs(lin);
+#pragma unroll
+                for (int j = 0; j < J; ++j) {
+                    if (j < jact) {
+                        const int bj = B0 + 32 * j + lane;
+                        const int r = t + s - bj;
+                        cells(j, znorm1(rows[r - 1], a, cw, isd), lin[j], r - w - 1 - (bj * K + 1));
+                        if (s == kCheckEvery - 1) bmin_a[j] = block_min(j);
+                        if (s == kCheckEvery) bmin_b[j] = block_min(j);
+                    }
+                }
             }
-            busy += kCheckEvery;
+            busy += kCheckEvery * jact;
             t += kCheckEvery;
-            dead_a = __ballot_sync(kFull, !(bmin_a <= ub));
+#pragma unroll
+            for (int j = 0; j < J; ++j)
+                dead_a[j] = (j < jact) ? __ballot_sync(kFull, !(bmin_a[j] <= ub)) : kFull;
             if (check(bmin_b, t)) break;
             continue;
         }
         // General step with per-lane range tests (pipeline fill and drain).
         ++t;
-        const int b = B0 + lane;
-        const int r = t - b;
-        float lin = __shfl_up_sync(kFull, lout, 1);
-        if (lane == 0) lin = INF;
         const int phase = t & (kCheckEvery - 1);
-        float bmin = INF;
-        if (r >= 1 && r <= nr) {
-            cells(znorm1(rows[r - 1], a, cw, isd), lin, r - w - 1 - (b * K + 1));
-            ++busy;
-            if (phase == 0 || phase == kCheckEvery - 1) bmin = block_min();
-        } else if (r < 1) {
-            lout = INF;
+        float lin[J], bmin[J];
+        left_inputs(lin);
+#pragma unroll
+        for (int j = 0; j < J; ++j) {
+            bmin[j] = INF;
+            if (j < jact) {
+                const int bj = B0 + 32 * j + lane;
+                const int r = t - bj;
+                if (r >= 1 && r <= nr) {
+                    cells(j, znorm1(rows[r - 1], a, cw, isd), lin[j], r - w - 1 - (bj * K + 1));
+                    ++busy;
+                    if (phase == 0 || phase == kCheckEvery - 1) bmin[j] = block_min(j);
+                } else {
+                    if (r < 1) lout[j] = INF;
+                    lprev[j] = lin[j];
+                }
+            }
         }
-        lprev = lin;
-
         if (t == t_end) {
             const int src = bm - B0;
             float fin = INF;
-            if (src >= 0 && src < 32) {
-                float mine = prv[0];
+            if (src >= 0 && src < 32 * jact) {
+                float mine = INF;
 #pragma unroll
-                for (int k = 1; k < K; ++k) mine = (k == km) ? prv[k] : mine;
-                fin = __shfl_sync(kFull, mine, src);
-            } else if (src >= 32) {
+                for (int j = 0; j < J; ++j) {
+                    if (j == (src >> 5)) {
+#pragma unroll
+                        for (int k = 0; k < K; ++k) mine = (k == km) ? prv[j][k] : mine;
+                    }
+                }
+                fin = __shfl_sync(kFull, mine, src & 31);
+            } else if (src >= 32 * jact) {
                 out.status = 1;
             }
             out.dist = fin;
@@ -236,7 +337,9 @@ __device__ __forceinline__ DtwOut dtw_warp(const float* __restrict__ rows, float
             break;
         }
         if (phase == kCheckEvery - 1) {
-            dead_a = __ballot_sync(kFull, !(bmin <= ub));
+#pragma unroll
+            for (int j = 0; j < J; ++j)
+                dead_a[j] = (j < jact) ? __ballot_sync(kFull, !(bmin[j] <= ub)) : kFull;
         } else if (phase == 0) {
             if (check(bmin, t)) break;
         }

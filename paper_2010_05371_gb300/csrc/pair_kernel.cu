@@ -14,7 +14,8 @@ __global__ void __launch_bounds__(32) pair_kernel(const float* __restrict__ rows
                                                   float ub, double* out) {
     if (!isnan(*out)) return;  // an earlier level finished
     BestSoFar fixed{nullptr, nullptr, 1, 1, ub};
-    const DtwOut o = dtw_warp<K, BAND>(rows, 0.0f, 0.0f, 1.0f, cols, nr, nc, w, fixed, ub);
+    const DtwOut o = dtw_warp<K, BAND, dtw_windows(K, BAND)>(rows, 0.0f, 0.0f, 1.0f, cols, nr, nc, w,
+                                                            fixed, ub);
     if (threadIdx.x == 0 && o.status == 0) {
         *out = (o.dist <= ub) ? static_cast<double>(o.dist)
                               : __longlong_as_double(0x7ff0000000000000ll);

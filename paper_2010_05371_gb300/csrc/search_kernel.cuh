@@ -69,14 +69,14 @@ __host__ inline size_t search_smem_bytes(int m) {
 #ifndef EAPDTW_MINB16
 #define EAPDTW_MINB16 3
 #endif
-__host__ __device__ constexpr int search_min_blocks(int K) {
-    return K <= 8 ? 4 : (K <= 16 ? EAPDTW_MINB16 : 2);
+__host__ __device__ constexpr int search_min_blocks(int K, int BAND) {
+    return dtw_windows(K, BAND) > 1 ? (K <= 4 ? 3 : 2) : (K <= 8 ? 4 : (K <= 16 ? EAPDTW_MINB16 : 2));
 }
 
 // LB: compile the lower-bound cascade in (true) or out (false, the "nolb"
 // variant and the list-mode re-runs); leaving it out frees registers.
 template <int K, int BAND, bool LB>
-__global__ void __launch_bounds__(kWarpsPerBlock * 32, search_min_blocks(K))
+__global__ void __launch_bounds__(kWarpsPerBlock * 32, search_min_blocks(K, BAND))
 search_kernel(const SearchArgs A) {
     extern __shared__ __align__(16) float smem[];
     const int m = A.q.m;
@@ -232,7 +232,8 @@ search_kernel(const SearchArgs A) {
                 if (lane == 0) count(kCntRecheck, 1);
                 continue;
             }
-            const DtwOut o = dtw_warp<K, BAND>(s_r + off, a_s, cw_s, isd_s, s_zq, m, m, A.w, A.bsf, ub);
+            const DtwOut o = dtw_warp<K, BAND, dtw_windows(K, BAND)>(s_r + off, a_s, cw_s, isd_s, s_zq, m,
+                                                                    m, A.w, A.bsf, ub);
             if (lane == 0) {
                 count(kCntSteps, static_cast<unsigned long long>(o.steps));
                 count(kCntCells, static_cast<unsigned long long>(o.busy) * K);
