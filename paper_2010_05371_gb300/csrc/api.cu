@@ -1,6 +1,7 @@
 // C ABI of the library (declared in include/eapdtw.h): argument checks, scratch
 // management and the launch sequence of eap_dtw and subseq_search.
 #include <cmath>
+#include <cstdio>
 #include <cstdint>
 #include <cstring>
 #include <mutex>
@@ -26,8 +27,9 @@ constexpr float kLbScale = 1.0001f;   // prune iff lb > ub * kLbScale (FP32 roun
 // region overflows the warp's window of 32 blocks are re-run with 2K, up to 32.
 struct Plan {
     int nlev = 0;
-    int K[kMaxLevels];
-    int band[kMaxLevels];
+    int K[kMaxLevels + 1];
+    int band[kMaxLevels + 1];
+    bool wide[kMaxLevels + 1];
 };
 
 Plan plan_levels(int64_t nr, int64_t nc, int64_t w, int tile_hint) {
@@ -53,8 +55,18 @@ Plan plan_levels(int64_t nr, int64_t nc, int64_t w, int tile_hint) {
         if (cols <= covered) continue;
         p.K[p.nlev] = K;
         p.band[p.nlev] = band;
+        p.wide[p.nlev] = false;
         ++p.nlev;
         covered = cols;
+    }
+    // Last level: four windows of 32-column blocks (4096 columns), needed only
+    // when the columns do not fit one window of K = 32 (an empty re-run list
+    // makes it a no-op launch).
+    if (nc > 32 * 32) {
+        p.K[p.nlev] = 32;
+        p.band[p.nlev] = unconstrained ? 0 : (32 <= 2 * w + 2 ? 1 : 2);
+        p.wide[p.nlev] = true;
+        ++p.nlev;
     }
     return p;
 }
@@ -106,14 +118,15 @@ struct Scratch {
 };
 
 enum IntSlot : int {
-    kWork0 = 0,      // work counters of levels 0..3
-    kWorkSeed = 4,
-    kOvf0 = 5,       // overflow counts written by levels 0..3
-    kBad = 9,
-    kNBest = 10,
-    kSeedOvf = 11,
+    kWork0 = 0,      // work counters of levels 0..kMaxLevels
+    kWorkSeed = kWork0 + kMaxLevels + 1,
+    kOvf0 = kWorkSeed + 1,  // overflow counts written by levels 0..kMaxLevels
+    kBad = kOvf0 + kMaxLevels + 1,
+    kNBest = kBad + 1,
+    kSeedOvf = kNBest + 1,
     kNumInts = 32
 };
+static_assert(kSeedOvf < kNumInts, "int slots");
 
 // (Re)allocate p with room for n elements (previous contents are dropped).
 template <typename T>
@@ -247,6 +260,7 @@ int32_t search_impl(Scratch& S, const float* Q, int64_t lQ, const float* R, int6
     a.use_lb = use_lb ? 1 : 0;
     a.lb_scale = kLbScale;
     a.counters = S.counters();
+    a.dbg = ints + 24;
 
     if (seed && !audit) {
         const int ns = static_cast<int>(nw < kSeedSamples ? nw : kSeedSamples);
@@ -264,7 +278,11 @@ int32_t search_impl(Scratch& S, const float* Q, int64_t lQ, const float* R, int6
         sa.counters = S.seed_counters();  // kept apart from the search's own counts
         const int K = plan.K[plan.nlev - 1];
         const int bd = plan.band[plan.nlev - 1];
-        CK(launch_search(K, bd, false, sa, search_blocks(K, bd, false, m) / 4 + 1, st));
+        if (plan.wide[plan.nlev - 1]) {
+            CK(launch_search_wide(bd, sa, search_blocks_wide(bd, m) / 4 + 1, st));
+        } else {
+            CK(launch_search(K, bd, false, sa, search_blocks(K, bd, false, m) / 4 + 1, st));
+        }
         launches += 3;
     }
     CK(cudaEventRecord(S.ev[2], st));
@@ -280,7 +298,12 @@ int32_t search_impl(Scratch& S, const float* Q, int64_t lQ, const float* R, int6
             la.ovf_in_cap = S.cap_ovf;
         }
         const bool lb = use_lb && lev == 0;
-        CK(launch_search(plan.K[lev], plan.band[lev], lb, la, search_blocks(plan.K[lev], plan.band[lev], lb, m), st));
+        if (plan.wide[lev]) {
+            CK(launch_search_wide(plan.band[lev], la, search_blocks_wide(plan.band[lev], m), st));
+        } else {
+            CK(launch_search(plan.K[lev], plan.band[lev], lb, la,
+                             search_blocks(plan.K[lev], plan.band[lev], lb, m), st));
+        }
         ++launches;
         if (lev == 0) CK(cudaEventRecord(S.ev[3], st));
     }
@@ -309,6 +332,12 @@ int32_t search_impl(Scratch& S, const float* Q, int64_t lQ, const float* R, int6
         opts->counters[EAPDTW_CNT_NS_TOTAL] = ns(0, 5);
         opts->counters[EAPDTW_CNT_LAUNCHES] = launches;
     }
+#ifdef EAPDTW_DEVICE_CHECKS
+    if (hi[24]) {
+        fprintf(stderr, "eapdtw device check failed: code %d value %d\n", hi[24], hi[25]);
+        return EAPDTW_ERR_INTERNAL;
+    }
+#endif
     if (hi[kBad]) return EAPDTW_ERR_NAN_INPUT;
     for (int lev = 0; lev + 1 < plan.nlev; ++lev)
         if (hi[kOvf0 + lev] > S.cap_ovf) return EAPDTW_ERR_INTERNAL;
@@ -369,8 +398,8 @@ int32_t eap_dtw(const float* S, int64_t lS, const float* T, int64_t lT, int64_t 
     const Plan plan = plan_levels(nr, nc, wi, 0);
     const float ubf = ub_to_f32_up(ub);
     for (int lev = 0; lev < plan.nlev; ++lev)
-        CK(launch_pair(plan.K[lev], plan.band[lev], rows, static_cast<int>(nr), cols,
-                       static_cast<int>(nc), wi, ubf, out_dist, nullptr, lev == plan.nlev - 1, st));
+        CK(launch_pair(plan.K[lev], plan.band[lev], plan.wide[lev], rows, static_cast<int>(nr), cols,
+                       static_cast<int>(nc), wi, ubf, out_dist, st));
     return EAPDTW_OK;
 }
 

@@ -175,6 +175,17 @@ __device__ __forceinline__ void window_coeffs(const RefView& ref, int64_t i, int
     }
 }
 
+// Optional device self-checks (build with -DEAPDTW_DEVICE_CHECKS): a failed
+// check records (code, value) in dbg[0..2] (first failure wins) and the caller
+// skips the access it guards.  Off by default.
+#ifdef EAPDTW_DEVICE_CHECKS
+#define EAPDTW_CHECK(dbg, ok, code, value)                                   \
+    ((ok) ? true                                                             \
+          : ((dbg) && atomicCAS((dbg), 0, (code)) == 0 ? ((dbg)[1] = (int)(value), false) : false))
+#else
+#define EAPDTW_CHECK(dbg, ok, code, value) true
+#endif
+
 __device__ __forceinline__ float znorm1(float x, float a, float cw, float isd) {
     return __fmul_rn(__fsub_rn(__fsub_rn(x, a), cw), isd);
 }

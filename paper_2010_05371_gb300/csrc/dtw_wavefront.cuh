@@ -81,17 +81,21 @@ __device__ __forceinline__ float f_nan() { return __int_as_float(0x7fffffff); }
 // BAND = 1: banded with K <= 2w + 2 (at most one forced cell per block and row);
 // BAND = 2: banded, any w (two forced cells may share a block).
 // J: windows of 32 blocks available to the live region.
+// CS: read the column values from `cols` at every step instead of holding them
+// in registers (for the widest windows, whose registers would not fit).
 // All 32 lanes call it with identical arguments.
-template <int K, int BAND, int J = 1>
+template <int K, int BAND, int J = 1, bool CS = false>
 __device__ __forceinline__ DtwOut dtw_warp(const float* __restrict__ rows, float a, float cw,
                                            float isd, const float* __restrict__ cols, int nr,
-                                           int nc, int w, const BestSoFar bsf, float ub) {
+                                           int nc, int w, const BestSoFar bsf, float ub,
+                                           int* dbg = nullptr) {
     static_assert(K % 4 == 0, "K must be a multiple of 4");
     static_assert(J >= 1 && J <= 4, "1 to 4 windows");
+    (void)dbg;
     const int lane = threadIdx.x & 31;
     const float INF = f_inf();
     float prv[J][K];
-    float zc[J][K];
+    float zc[CS ? 1 : J][K];
     float lout[J];    // each window's last cell of this lane's block, previous step
     float lprev[J];   // left input of the previous step (diagonal of cell 0)
     float omin[J];    // min of lout since the last check
@@ -99,19 +103,23 @@ __device__ __forceinline__ DtwOut dtw_warp(const float* __restrict__ rows, float
     int B0 = 0;
     int jact = 1;     // active windows
 
-    auto load_cols = [&](int j) {
+    // Column values of window j's block into q[0..K) (+NaN past the last column).
+    auto fetch_cols = [&](int j, float* q) {
         const int cb = (B0 + 32 * j + lane) * K;
         if (cb + K <= nc && (reinterpret_cast<uintptr_t>(cols + cb) & 15) == 0) {
             const float4* p = reinterpret_cast<const float4*>(cols + cb);
 #pragma unroll
-            for (int q = 0; q < K / 4; ++q) {
-                const float4 v = p[q];
-                zc[j][4 * q] = v.x; zc[j][4 * q + 1] = v.y; zc[j][4 * q + 2] = v.z; zc[j][4 * q + 3] = v.w;
+            for (int u = 0; u < K / 4; ++u) {
+                const float4 v = p[u];
+                q[4 * u] = v.x; q[4 * u + 1] = v.y; q[4 * u + 2] = v.z; q[4 * u + 3] = v.w;
             }
         } else {
 #pragma unroll
-            for (int k = 0; k < K; ++k) zc[j][k] = (cb + k < nc) ? cols[cb + k] : f_nan();
+            for (int k = 0; k < K; ++k) q[k] = (cb + k < nc) ? cols[cb + k] : f_nan();
         }
+    };
+    auto load_cols = [&](int j) {
+        if (!CS) fetch_cols(j, zc[CS ? 0 : j]);
     };
     auto reset = [&](int j) {
 #pragma unroll
@@ -128,6 +136,10 @@ __device__ __forceinline__ DtwOut dtw_warp(const float* __restrict__ rows, float
     }
     if (lane == 0) lprev[0] = 0.0f;   // D(0,0) = 0: diagonal of cell (1,1)
 
+    // A cell is alive iff v <= ub.  +inf marks cells that do not exist (the
+    // border, out-of-band cells, retired blocks), so ub is kept finite: with
+    // ub = +inf, a +inf cell would otherwise count as alive.
+    ub = fminf(ub, 3.402823466e38f);
     float ub_next = ub;
     const int bm = (nc - 1) / K;       // block of the last column
     const int km = (nc - 1) - bm * K;
@@ -151,6 +163,8 @@ __device__ __forceinline__ DtwOut dtw_warp(const float* __restrict__ rows, float
     // the position, in the block, of the column just left of the band (the one
     // just right of it is f1 + 2w + 2); both are forced to +inf.
     auto cells = [&](int j, float z, float lin, int f1) {
+        float qs[CS ? K : 1];
+        if (CS) fetch_cols(j, qs);
         float diag = lprev[j];
         float left = lin;
         int kf = -1, kf2 = -1;
@@ -162,7 +176,7 @@ __device__ __forceinline__ DtwOut dtw_warp(const float* __restrict__ rows, float
 #pragma unroll
         for (int k = 0; k < K; ++k) {
             const float top = prv[j][k];
-            const float d = __fsub_rn(z, zc[j][k]);
+            const float d = __fsub_rn(z, CS ? qs[CS ? k : 0] : zc[CS ? 0 : j][k]);
             float v = __fmaf_rn(d, d, fminf(fminf(top, diag), left));
             if (BAND == 1) v = (k == kf) ? INF : v;
             if (BAND == 2) v = (k == kf || k == kf2) ? INF : v;
@@ -184,6 +198,13 @@ __device__ __forceinline__ DtwOut dtw_warp(const float* __restrict__ rows, float
     // dead_a holds the dead lanes of the step before.  Returns true when the
     // candidate is finished (abandoned or overflowed).
     auto check = [&](const float* bmin_b, int t) -> bool {
+#ifdef EAPDTW_DEVICE_CHECKS
+        EAPDTW_CHECK(dbg, __shfl_sync(kFull, t, 0) == t, 13, t);
+        EAPDTW_CHECK(dbg, __shfl_sync(kFull, B0, 0) == B0, 14, B0);
+        EAPDTW_CHECK(dbg, __shfl_sync(kFull, jact, 0) == jact, 15, jact);
+        EAPDTW_CHECK(dbg, __shfl_sync(kFull, __float_as_int(ub), 0) == __float_as_int(ub), 16, 0);
+        EAPDTW_CHECK(dbg, __shfl_sync(kFull, __float_as_int(ub_next), 0) == __float_as_int(ub_next), 17, 0);
+#endif
         ub = fminf(ub, ub_next);
         unsigned db[J];
 #pragma unroll
@@ -235,7 +256,7 @@ __device__ __forceinline__ DtwOut dtw_warp(const float* __restrict__ rows, float
                 --jact;
             }
         }
-        ub_next = bsf.load();
+        ub_next = __shfl_sync(kFull, bsf.load(), 0);  // one reading for the whole warp
 #pragma unroll
         for (int j = 0; j < J; ++j) omin[j] = INF;
         if (d > 0) {
@@ -281,7 +302,8 @@ __device__ __forceinline__ DtwOut dtw_warp(const float* __restrict__ rows, float
                     if (j < jact) {
                         const int bj = B0 + 32 * j + lane;
                         const int r = t + s - bj;
-                        cells(j, znorm1(rows[r - 1], a, cw, isd), lin[j], r - w - 1 - (bj * K + 1));
+                        const float x = EAPDTW_CHECK(dbg, r >= 1 && r <= nr, 11, r) ? rows[r - 1] : 0.0f;
+                        cells(j, znorm1(x, a, cw, isd), lin[j], r - w - 1 - (bj * K + 1));
                         if (s == kCheckEvery - 1) bmin_a[j] = block_min(j);
                         if (s == kCheckEvery) bmin_b[j] = block_min(j);
                     }
@@ -307,7 +329,8 @@ __device__ __forceinline__ DtwOut dtw_warp(const float* __restrict__ rows, float
                 const int bj = B0 + 32 * j + lane;
                 const int r = t - bj;
                 if (r >= 1 && r <= nr) {
-                    cells(j, znorm1(rows[r - 1], a, cw, isd), lin[j], r - w - 1 - (bj * K + 1));
+                    const float x = EAPDTW_CHECK(dbg, r - 1 < nr, 12, r) ? rows[r - 1] : 0.0f;
+                    cells(j, znorm1(x, a, cw, isd), lin[j], r - w - 1 - (bj * K + 1));
                     ++busy;
                     if (phase == 0 || phase == kCheckEvery - 1) bmin[j] = block_min(j);
                 } else {

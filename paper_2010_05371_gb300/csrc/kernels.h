@@ -29,9 +29,12 @@ cudaError_t launch_finalize(const unsigned long long* slots, int k, int64_t* out
 // persistent grid (resident blocks per SM x SMs).
 cudaError_t launch_search(int K, int band, bool lb, const SearchArgs& args, int blocks, cudaStream_t s);
 int search_blocks(int K, int band, bool lb, int m);
+// The widest re-run level (K = 32, four windows, 4096 columns).
+cudaError_t launch_search_wide(int band, const SearchArgs& args, int blocks, cudaStream_t s);
+int search_blocks_wide(int band, int m);
 
-// eap_dtw single pair: one warp.
-cudaError_t launch_pair(int K, int band, const float* rows, int nr, const float* cols, int nc, int w,
-                        float ub, double* out, int* ovf_flag, int final_level, cudaStream_t s);
+// eap_dtw single pair: one warp; wide selects the four-window level.
+cudaError_t launch_pair(int K, int band, bool wide, const float* rows, int nr, const float* cols, int nc,
+                        int w, float ub, double* out, cudaStream_t s);
 
 }  // namespace eapdtw

@@ -44,7 +44,7 @@ constexpr int64_t kOffSeedBest = kOffSeedIdx + al(4 * kSeedN);
 constexpr int64_t kUsed = kOffSeedBest + al(4 * 64);
 static_assert(kUsed <= EAPDTW_NOALLOC_SCRATCH_BYTES, "scratch layout exceeds the declared size");
 
-enum : int { kWork0 = 0, kWorkSeed = 4, kOvf0 = 5, kBad = 9, kNBest = 10, kSeedOvf = 11, kInts = 32 };
+enum : int { kWork0 = 0, kWorkSeed = 5, kOvf0 = 6, kBad = 11, kNBest = 12, kSeedOvf = 13, kInts = 32 };
 
 __device__ __align__(256) unsigned char g_scratch[EAPDTW_NOALLOC_SCRATCH_BYTES];
 
@@ -60,8 +60,9 @@ unsigned char* g_addr[64] = {nullptr};  // device address of g_scratch, per devi
     } while (0)
 
 // The window of blocks per warp, as subseq_search plans it (first level K,
-// then 2K up to 32 for windows whose live region overflowed).
-int plan(int m, int w, int* K, int* band) {
+// then 2K up to 32 for windows whose live region overflowed, then the
+// four-window level when the query is wider than 1024 columns).
+int plan(int m, int w, int* K, int* band, bool* wide) {
     const bool unconstrained = w >= m - 1;
     int k0 = 32;
     if (!unconstrained) {
@@ -76,6 +77,13 @@ int plan(int m, int w, int* K, int* band) {
     for (int k = k0; k <= 32; k *= 2) {
         K[n] = k;
         band[n] = unconstrained ? 0 : (k <= 2 * w + 2 ? 1 : 2);
+        wide[n] = false;
+        ++n;
+    }
+    if (m > 32 * 32) {
+        K[n] = 32;
+        band[n] = unconstrained ? 0 : (32 <= 2 * w + 2 ? 1 : 2);
+        wide[n] = true;
         ++n;
     }
     return n;
@@ -137,8 +145,9 @@ extern "C" int32_t subseq_search_noalloc(const float* Q, int64_t lQ, const float
     int* seed_best = reinterpret_cast<int*>(base + kOffSeedBest);
     const int ovf_cap = static_cast<int>(nw);
 
-    int Ks[4], bands[4];
-    const int nlev = plan(m, wi, Ks, bands);
+    int Ks[5], bands[5];
+    bool wides[5];
+    const int nlev = plan(m, wi, Ks, bands, wides);
 
     // the previous call's state is overwritten here: slots, counters, work lists
     CKN(launch_init_state(slots, k, ub_seed, counters, ints, kInts, st));
@@ -173,7 +182,11 @@ extern "C" int32_t subseq_search_noalloc(const float* Q, int64_t lQ, const float
         sa.ovf_cap = 0;
         sa.counters = seed_counters;
         const int K = Ks[nlev - 1], bd = bands[nlev - 1];
-        CKN(launch_search(K, bd, false, sa, search_blocks(K, bd, false, m) / 4 + 1, st));
+        if (wides[nlev - 1]) {
+            CKN(launch_search_wide(bd, sa, search_blocks_wide(bd, m) / 4 + 1, st));
+        } else {
+            CKN(launch_search(K, bd, false, sa, search_blocks(K, bd, false, m) / 4 + 1, st));
+        }
     }
     for (int lev = 0; lev < nlev; ++lev) {
         SearchArgs la = a;
@@ -187,7 +200,11 @@ extern "C" int32_t subseq_search_noalloc(const float* Q, int64_t lQ, const float
             la.ovf_in_cap = ovf_cap;
         }
         const bool lb = lev == 0;
-        CKN(launch_search(Ks[lev], bands[lev], lb, la, search_blocks(Ks[lev], bands[lev], lb, m), st));
+        if (wides[lev]) {
+            CKN(launch_search_wide(bands[lev], la, search_blocks_wide(bands[lev], m), st));
+        } else {
+            CKN(launch_search(Ks[lev], bands[lev], lb, la, search_blocks(Ks[lev], bands[lev], lb, m), st));
+        }
     }
     CKN(launch_finalize(slots, k, out_idx, out_dist, st));
     int hi[kInts];

@@ -8,14 +8,14 @@ namespace eapdtw {
 // *out holds NaN until some level succeeds.  A level whose live region
 // overflows its window of blocks leaves NaN for the next (wider) level; the
 // last level leaves NaN if it overflows too.
-template <int K, int BAND>
+template <int K, int BAND, bool WIDE>
 __global__ void __launch_bounds__(32) pair_kernel(const float* __restrict__ rows, int nr,
                                                   const float* __restrict__ cols, int nc, int w,
                                                   float ub, double* out) {
     if (!isnan(*out)) return;  // an earlier level finished
     BestSoFar fixed{nullptr, nullptr, 1, 1, ub};
-    const DtwOut o = dtw_warp<K, BAND, dtw_windows(K, BAND)>(rows, 0.0f, 0.0f, 1.0f, cols, nr, nc, w,
-                                                            fixed, ub);
+    constexpr int kJ = WIDE ? 4 : dtw_windows(K, BAND);
+    const DtwOut o = dtw_warp<K, BAND, kJ, WIDE>(rows, 0.0f, 0.0f, 1.0f, cols, nr, nc, w, fixed, ub);
     if (threadIdx.x == 0 && o.status == 0) {
         *out = (o.dist <= ub) ? static_cast<double>(o.dist)
                               : __longlong_as_double(0x7ff0000000000000ll);
@@ -23,23 +23,24 @@ __global__ void __launch_bounds__(32) pair_kernel(const float* __restrict__ rows
 }
 
 namespace {
-template <int K>
+template <int K, bool WIDE>
 cudaError_t launch_k(int band, const float* rows, int nr, const float* cols, int nc, int w, float ub,
                      double* out, cudaStream_t s) {
-    if (band == 0) pair_kernel<K, 0><<<1, 32, 0, s>>>(rows, nr, cols, nc, w, ub, out);
-    else if (band == 1) pair_kernel<K, 1><<<1, 32, 0, s>>>(rows, nr, cols, nc, w, ub, out);
-    else pair_kernel<K, 2><<<1, 32, 0, s>>>(rows, nr, cols, nc, w, ub, out);
+    if (band == 0) pair_kernel<K, 0, WIDE><<<1, 32, 0, s>>>(rows, nr, cols, nc, w, ub, out);
+    else if (band == 1) pair_kernel<K, 1, WIDE><<<1, 32, 0, s>>>(rows, nr, cols, nc, w, ub, out);
+    else pair_kernel<K, 2, WIDE><<<1, 32, 0, s>>>(rows, nr, cols, nc, w, ub, out);
     return cudaGetLastError();
 }
 }  // namespace
 
-cudaError_t launch_pair(int K, int band, const float* rows, int nr, const float* cols, int nc, int w,
-                        float ub, double* out, int* /*unused*/, int /*unused*/, cudaStream_t s) {
+cudaError_t launch_pair(int K, int band, bool wide, const float* rows, int nr, const float* cols, int nc,
+                        int w, float ub, double* out, cudaStream_t s) {
+    if (wide) return launch_k<32, true>(band, rows, nr, cols, nc, w, ub, out, s);
     switch (K) {
-        case 4: return launch_k<4>(band, rows, nr, cols, nc, w, ub, out, s);
-        case 8: return launch_k<8>(band, rows, nr, cols, nc, w, ub, out, s);
-        case 16: return launch_k<16>(band, rows, nr, cols, nc, w, ub, out, s);
-        default: return launch_k<32>(band, rows, nr, cols, nc, w, ub, out, s);
+        case 4: return launch_k<4, false>(band, rows, nr, cols, nc, w, ub, out, s);
+        case 8: return launch_k<8, false>(band, rows, nr, cols, nc, w, ub, out, s);
+        case 16: return launch_k<16, false>(band, rows, nr, cols, nc, w, ub, out, s);
+        default: return launch_k<32, false>(band, rows, nr, cols, nc, w, ub, out, s);
     }
 }
 

@@ -44,6 +44,7 @@ struct SearchArgs {
     const int* ovf_in;        // list mode input
     const int* ovf_in_count;
     int ovf_in_cap;           // entries beyond the capacity were dropped by the producer
+    int* dbg;                 // device self-check record (EAPDTW_DEVICE_CHECKS builds only)
 };
 
 __host__ __device__ inline int query_pad(int m) { return (m + kLbUnroll - 1) / kLbUnroll * kLbUnroll; }
@@ -75,8 +76,11 @@ __host__ __device__ constexpr int search_min_blocks(int K, int BAND) {
 
 // LB: compile the lower-bound cascade in (true) or out (false, the "nolb"
 // variant and the list-mode re-runs); leaving it out frees registers.
-template <int K, int BAND, bool LB>
-__global__ void __launch_bounds__(kWarpsPerBlock * 32, search_min_blocks(K, BAND))
+// WIDE: the last re-run level for the widest live regions: four windows of 32
+// blocks of K columns (4096 columns at K = 32), the column values streamed from
+// shared memory, one resident block per SM.
+template <int K, int BAND, bool LB, bool WIDE = false>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32, WIDE ? 1 : search_min_blocks(K, BAND))
 search_kernel(const SearchArgs A) {
     extern __shared__ __align__(16) float smem[];
     const int m = A.q.m;
@@ -128,6 +132,7 @@ search_kernel(const SearchArgs A) {
         }
         // Stage R[i0 .. i0 + nlanes - 1 + m) into the warp's tile.
         const int len = nlanes - 1 + m;
+        if (!EAPDTW_CHECK(A.dbg, len <= tile_floats(m) && i0 >= 0 && i0 + len <= A.ref.n, 21, len)) break;
         if (r_aligned && !list_mode) {
             const float4* src = reinterpret_cast<const float4*>(A.ref.R + i0);
             const int nv = len / 4;
@@ -168,7 +173,7 @@ search_kernel(const SearchArgs A) {
 #pragma unroll
                     for (int u = 0; u < kLbUnroll; ++u) {
                         const int j = s_ord[p + u];
-                        const float z = znorm1(x[j], a, cw, isd);
+                        const float z = znorm1(EAPDTW_CHECK(A.dbg, j >= 0 && j < m, 22, j) ? x[j] : 0.0f, a, cw, isd);
                         const float e = fmaxf(fmaxf(__fsub_rn(z, s_uq[p + u]), __fsub_rn(s_lq[p + u], z)), 0.0f);
                         s = __fmaf_rn(e, e, s);
                     }
@@ -187,8 +192,9 @@ search_kernel(const SearchArgs A) {
 #pragma unroll
                         for (int u = 0; u < kLbUnroll; ++u) {
                             const int j = s_ord[p + u];
-                            const float uu = znorm1(__ldg(ur + j), a, cw, isd);
-                            const float ll = znorm1(__ldg(lr + j), a, cw, isd);
+                            const bool okj = EAPDTW_CHECK(A.dbg, j >= 0 && j < m && i + j < A.ref.n, 23, j);
+                            const float uu = znorm1(okj ? __ldg(ur + j) : 0.0f, a, cw, isd);
+                            const float ll = znorm1(okj ? __ldg(lr + j) : 0.0f, a, cw, isd);
                             const float qv = s_zqo[p + u];
                             const float e = fmaxf(fmaxf(__fsub_rn(qv, uu), __fsub_rn(ll, qv)), 0.0f);
                             s2 = __fmaf_rn(e, e, s2);
@@ -227,13 +233,22 @@ search_kernel(const SearchArgs A) {
             const float lb_s = __shfl_sync(kFull, lb, src);
             const int off = list_mode ? 0 : src;
             const int64_t iw = i0 + off;
-            float ub = A.bsf.load();
+            // ub steers warp-wide control flow (the recheck below skips the
+            // DTW for the whole warp): take lane 0's reading, because other
+            // warps lower the bound concurrently and lanes that load it at
+            // slightly different times may see different values.
+            float ub = __shfl_sync(kFull, A.bsf.load(), 0);
+#ifdef EAPDTW_DEVICE_CHECKS
+            EAPDTW_CHECK(A.dbg, __shfl_sync(kFull, __float_as_int(ub), 0) == __float_as_int(ub), 24, 0);
+            EAPDTW_CHECK(A.dbg, off >= 0 && off < 32 && iw < A.nw, 25, off);
+#endif
             if (LB && A.use_lb && !list_mode && lb_s > ub * A.lb_scale) {
                 if (lane == 0) count(kCntRecheck, 1);
                 continue;
             }
-            const DtwOut o = dtw_warp<K, BAND, dtw_windows(K, BAND)>(s_r + off, a_s, cw_s, isd_s, s_zq, m,
-                                                                    m, A.w, A.bsf, ub);
+            constexpr int kJ = WIDE ? 4 : dtw_windows(K, BAND);
+            const DtwOut o = dtw_warp<K, BAND, kJ, WIDE>(s_r + off, a_s, cw_s, isd_s, s_zq, m, m, A.w,
+                                                         A.bsf, ub, A.dbg);
             if (lane == 0) {
                 count(kCntSteps, static_cast<unsigned long long>(o.steps));
                 count(kCntCells, static_cast<unsigned long long>(o.busy) * K);
@@ -246,8 +261,8 @@ search_kernel(const SearchArgs A) {
                 }
                 continue;
             }
-            ub = A.bsf.load();
-            if (o.dist <= ub) {
+            ub = __shfl_sync(kFull, A.bsf.load(), 0);
+            if (o.dist <= ub && o.dist < f_inf()) {
                 if (lane == 0) {
                     A.bsf.insert(o.dist, static_cast<uint32_t>(iw));
                     count(kCntCompleted, 1);

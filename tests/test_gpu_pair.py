@@ -82,3 +82,18 @@ def test_ties_are_not_abandoned():
         assert api.eap_dtw(dev(S), dev(T), 5, d).item() == d
         if d > 0:
             assert math.isinf(api.eap_dtw(dev(S), dev(T), 5, d - 0.5).item())
+
+
+@pytest.mark.parametrize("n,m,w", [(1100, 1100, None), (2500, 2300, None), (4000, 4000, None),
+                                   (3000, 3000, 800), (3500, 3100, 1500)])
+def test_wide_live_region(n, m, w):
+    """ub = +inf keeps every cell alive: the live region is the whole band, wider
+    than one window of K = 32 blocks, so the four-window level must finish it."""
+    rng = np.random.default_rng(n + m)
+    S = f32(np.cumsum(rng.standard_normal(n)) * 0.05)
+    T = f32(np.cumsum(rng.standard_normal(m)) * 0.05)
+    d = O.dtw(S, T, w)
+    got = api.eap_dtw(dev(S), dev(T), w, math.inf).item()
+    assert dist_close(got, d, max(n, m)), (got, d)
+    got2 = api.eap_dtw(dev(S), dev(T), w, d * 1.01).item()
+    assert dist_close(got2, d, max(n, m))

@@ -134,3 +134,15 @@ def test_repeatable_and_seed_independent():
     c = run(Q, R, 20, 5, no_seed=True)
     assert list(a[0]) == list(b[0]) == list(c[0])
     assert list(a[1]) == list(b[1]) == list(c[1])
+
+
+def test_wide_query_without_seed():
+    """m = 1500, unconstrained, no seed: the first candidates run with ub = +inf,
+    their live regions exceed 1024 columns and go to the four-window level."""
+    R = synth.random_walk(2500, 31)
+    Q = synth.random_walk(1500, 32)
+    oi, od = O.search_brute(Q, R, 1500, 2)
+    gi, gd = run(Q, R, 1500, 2, no_seed=True, no_lb=True)
+    check_topk(gi, gd, oi, od, Q, R, 1500)
+    gi, gd = run(Q, R, 1500, 2, no_seed=True)
+    check_topk(gi, gd, oi, od, Q, R, 1500)
