@@ -182,7 +182,7 @@ int32_t eapdtw_release_scratch(void);
  *   would race on the array.
  */
 #define EAPDTW_NOALLOC_MAX_N (1 << 20)
-#define EAPDTW_NOALLOC_SCRATCH_BYTES (32 * (int64_t)EAPDTW_NOALLOC_MAX_N + (1 << 20))
+#define EAPDTW_NOALLOC_SCRATCH_BYTES (40 * (int64_t)EAPDTW_NOALLOC_MAX_N + (1 << 20))
 int32_t subseq_search_noalloc(const float* Q, int64_t lQ, const float* R, int64_t lR, int64_t w,
                               int32_t k, int64_t* out_idx, double* out_dist, void* stream);
 

@@ -98,9 +98,9 @@ struct Scratch {
     // seed
     float* seed_ed = nullptr;
     int* seed_idx = nullptr;
-    int* seed_best = nullptr;
+    long long* seed_best = nullptr;
     // overflow lists
-    int* ovf[2] = {nullptr, nullptr};
+    long long* ovf[2] = {nullptr, nullptr};
     int cap_ovf = 0;
     // host-pointer entry points
     float *dQ = nullptr, *dR = nullptr;
@@ -163,7 +163,7 @@ Scratch* scratch_for_current_device(int* dev_out) {
             cudaMallocHost(reinterpret_cast<void**>(&s->host_state), 1024) != cudaSuccess ||
             cudaMalloc(reinterpret_cast<void**>(&s->seed_ed), sizeof(float) * kSeedSamples) != cudaSuccess ||
             cudaMalloc(reinterpret_cast<void**>(&s->seed_idx), sizeof(int) * kSeedSamples) != cudaSuccess ||
-            cudaMalloc(reinterpret_cast<void**>(&s->seed_best), sizeof(int) * 64) != cudaSuccess) {
+            cudaMalloc(reinterpret_cast<void**>(&s->seed_best), sizeof(long long) * 64) != cudaSuccess) {
             cudaGetLastError();
             delete s;
             return nullptr;

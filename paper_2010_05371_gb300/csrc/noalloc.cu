@@ -28,8 +28,8 @@ constexpr int64_t kOffP2 = kOffP1 + al(8 * kMaxN);
 constexpr int64_t kOffUR = kOffP2 + al(8 * kMaxN);
 constexpr int64_t kOffLR = kOffUR + al(4 * kMaxN);
 constexpr int64_t kOffOvf0 = kOffLR + al(4 * kMaxN);
-constexpr int64_t kOffOvf1 = kOffOvf0 + al(4 * kMaxN);
-constexpr int64_t kOffT1 = kOffOvf1 + al(4 * kMaxN);
+constexpr int64_t kOffOvf1 = kOffOvf0 + al(8 * kMaxN);
+constexpr int64_t kOffT1 = kOffOvf1 + al(8 * kMaxN);
 constexpr int64_t kOffT2 = kOffT1 + al(8 * kMaxChunks);
 constexpr int64_t kOffA = kOffT2 + al(8 * kMaxChunks);
 constexpr int64_t kOffZq = kOffA + al(4 * kMaxChunks);
@@ -41,7 +41,7 @@ constexpr int64_t kOffState = kOffOrd + al(4 * kMaxQ);   // slots | counters | s
 constexpr int64_t kOffSeedEd = kOffState + 1024;
 constexpr int64_t kOffSeedIdx = kOffSeedEd + al(4 * kSeedN);
 constexpr int64_t kOffSeedBest = kOffSeedIdx + al(4 * kSeedN);
-constexpr int64_t kUsed = kOffSeedBest + al(4 * 64);
+constexpr int64_t kUsed = kOffSeedBest + al(8 * 64);
 static_assert(kUsed <= EAPDTW_NOALLOC_SCRATCH_BYTES, "scratch layout exceeds the declared size");
 
 enum : int { kWork0 = 0, kWorkSeed = 5, kOvf0 = 6, kBad = 11, kNBest = 12, kSeedOvf = 13, kInts = 32 };
@@ -128,7 +128,7 @@ extern "C" int32_t subseq_search_noalloc(const float* Q, int64_t lQ, const float
     float* A = reinterpret_cast<float*>(base + kOffA);
     float* UR = reinterpret_cast<float*>(base + kOffUR);
     float* LR = reinterpret_cast<float*>(base + kOffLR);
-    int* ovf[2] = {reinterpret_cast<int*>(base + kOffOvf0), reinterpret_cast<int*>(base + kOffOvf1)};
+    long long* ovf[2] = {reinterpret_cast<long long*>(base + kOffOvf0), reinterpret_cast<long long*>(base + kOffOvf1)};
     float* zq = reinterpret_cast<float*>(base + kOffZq);
     float* uq = reinterpret_cast<float*>(base + kOffUq);
     float* lq = reinterpret_cast<float*>(base + kOffLq);
@@ -142,7 +142,7 @@ extern "C" int32_t subseq_search_noalloc(const float* Q, int64_t lQ, const float
     float* ub_seed = reinterpret_cast<float*>(state + 896);
     float* seed_ed = reinterpret_cast<float*>(base + kOffSeedEd);
     int* seed_idx = reinterpret_cast<int*>(base + kOffSeedIdx);
-    int* seed_best = reinterpret_cast<int*>(base + kOffSeedBest);
+    long long* seed_best = reinterpret_cast<long long*>(base + kOffSeedBest);
     const int ovf_cap = static_cast<int>(nw);
 
     int Ks[5], bands[5];

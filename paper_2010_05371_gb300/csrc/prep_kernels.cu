@@ -304,7 +304,7 @@ __global__ void seed_ed_kernel(const RefView ref, const float* __restrict__ zq, 
 // cannot place it below the DTW of its own window; also writes the windows of
 // the `nbest` smallest samples (for an exact DTW pass that seeds the k-best list).
 __global__ void __launch_bounds__(1024) seed_select_kernel(const float* ed, const int* idx, int ns, int k,
-                                                           float* ub_seed, int* best, int nbest,
+                                                           float* ub_seed, long long* best, int nbest,
                                                            int* nbest_out) {
     __shared__ float s_v[64];
     __shared__ int s_i[64];
@@ -404,7 +404,7 @@ cudaError_t launch_init_state(unsigned long long* slots, int k, float* ub_seed,
 }
 
 cudaError_t launch_seed(const RefView& ref, const float* zq, int m, int64_t nw, int nsamples,
-                        float* ed, int* idx, int k, float* ub_seed, int* best, int nbest,
+                        float* ed, int* idx, int k, float* ub_seed, long long* best, int nbest,
                         int* nbest_out, cudaStream_t s) {
     const int threads = 256;
     const int blocks = (nsamples * 32 + threads - 1) / threads;

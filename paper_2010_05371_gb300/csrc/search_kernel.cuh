@@ -38,10 +38,10 @@ struct SearchArgs {
     float lb_scale;    // prune iff lb > ub * lb_scale (lb_scale = 1 + slack)
     int* work_counter; // tile / list-item counter
     unsigned long long* counters;
-    int* ovf_out;      // windows whose live region overflowed (re-run wider)
+    long long* ovf_out;  // windows whose live region overflowed (re-run wider)
     int* ovf_out_count;
     int ovf_cap;
-    const int* ovf_in;        // list mode input
+    const long long* ovf_in;  // list mode input
     const int* ovf_in_count;
     int ovf_in_cap;           // entries beyond the capacity were dropped by the producer
     int* dbg;                 // device self-check record (EAPDTW_DEVICE_CHECKS builds only)
@@ -63,6 +63,186 @@ __host__ inline int search_warps(int m) {
 __host__ inline size_t search_smem_bytes(int m) {
     const int mp = query_pad(m);
     return sizeof(float) * (5 * static_cast<size_t>(mp) + search_warps(m) * static_cast<size_t>(tile_floats(m)));
+}
+
+// Everything one work item needs: where the reference, the query and the
+// best-so-far bound live.  The query arrays may be in shared memory (one
+// query per launch) or in global memory (a batch of queries).
+struct TileCtx {
+    RefView ref;
+    const float* zq;      // [>= m] z-normalised query (NaN past m)
+    const float* uq;      // [mp] LB order
+    const float* lq;
+    const float* zqo;
+    const int* ord;
+    int m;
+    int w;
+    int use_lb;           // LB_Kim and LB_Keogh EQ
+    int use_ec;           // LB_Keogh EC (needs ur / lr)
+    const float* ur;
+    const float* lr;
+    float lb_scale;
+    BestSoFar bsf;
+    int64_t nw;
+    long long* ovf_out;   // overflow list: entries (tag | window)
+    int* ovf_out_count;
+    int ovf_cap;
+    long long tag;        // high bits of the overflow entries (batch item << 32)
+    int* dbg;
+};
+
+// One work item on one warp: a tile of nlanes (<= 32) consecutive windows
+// starting at i0, or (list_mode) the single window i0.  Stages the windows'
+// points into the warp's shared-memory tile s_r, runs the lower bounds lane by
+// lane (tile mode), then EAPrunedDTW for every survivor on the whole warp.
+template <int K, int BAND, bool LB, bool WIDE, typename CountF>
+__device__ __forceinline__ void process_tile(const TileCtx& C, float* s_r, bool list_mode, int64_t i0,
+                                             int nlanes, CountF count) {
+    const int lane = threadIdx.x & 31;
+    const int m = C.m;
+    const int mp = query_pad(m);
+    // Stage R[i0 .. i0 + nlanes - 1 + m) into the warp's tile.
+    const int len = nlanes - 1 + m;
+    if (!EAPDTW_CHECK(C.dbg, len <= tile_floats(m) && i0 >= 0 && i0 + len <= C.ref.n, 21, len)) return;
+    if ((reinterpret_cast<uintptr_t>(C.ref.R + i0) & 15) == 0 && !list_mode) {
+        const float4* src = reinterpret_cast<const float4*>(C.ref.R + i0);
+        const int nv = len / 4;
+        for (int v = lane; v < nv; v += 32) reinterpret_cast<float4*>(s_r)[v] = __ldg(src + v);
+        for (int j = nv * 4 + lane; j < len; j += 32) s_r[j] = __ldg(C.ref.R + i0 + j);
+    } else {
+        for (int j = lane; j < len; j += 32) s_r[j] = __ldg(C.ref.R + i0 + j);
+    }
+    __syncwarp();
+
+    // ---- per-lane window statistics and lower bounds ----------------------
+    const int my = list_mode ? 0 : lane;
+    const bool valid = lane < nlanes || list_mode;
+    const int64_t i = i0 + my;
+    float a = 0.0f, cw = 0.0f, isd = 0.0f;
+    if (valid) window_coeffs(C.ref, i, m, s_r + my, a, cw, isd);
+    float lb = 0.0f;
+    bool alive = valid && (!list_mode || lane == 0);
+    int why = 0;  // 1, 2, 3: pruned by LB_Kim, LB_Keogh EQ, LB_Keogh EC
+    if (LB && C.use_lb && alive && !list_mode) {
+        const float ub = C.bsf.load() * C.lb_scale;
+        const float* x = s_r + my;
+        const float z0 = znorm1(x[0], a, cw, isd);
+        const float d0 = __fsub_rn(z0, C.zq[0]);
+        float kim = __fmul_rn(d0, d0);
+        if (m > 1) {
+            const float dl = __fsub_rn(znorm1(x[m - 1], a, cw, isd), C.zq[m - 1]);
+            kim = __fmaf_rn(dl, dl, kim);
+        }
+        lb = kim;
+        if (kim > ub) {
+            alive = false;
+            why = 1;
+        } else {
+            // LB_Keogh EQ: the normalised window against the query envelope.
+            float s = 0.0f;
+            for (int p = 0; p < mp; p += kLbUnroll) {
+#pragma unroll
+                for (int u = 0; u < kLbUnroll; ++u) {
+                    const int j = C.ord[p + u];
+                    const float z = znorm1(EAPDTW_CHECK(C.dbg, j >= 0 && j < m, 22, j) ? x[j] : 0.0f, a, cw, isd);
+                    const float e = fmaxf(fmaxf(__fsub_rn(z, C.uq[p + u]), __fsub_rn(C.lq[p + u], z)), 0.0f);
+                    s = __fmaf_rn(e, e, s);
+                }
+                if (s > ub) break;
+            }
+            lb = fmaxf(lb, s);
+            if (s > ub) {
+                alive = false;
+                why = 2;
+            } else if (C.use_ec) {
+                // LB_Keogh EC: the query against the window's envelope.
+                float s2 = 0.0f;
+                const float* ur = C.ur + i;
+                const float* lr = C.lr + i;
+                for (int p = 0; p < mp; p += kLbUnroll) {
+#pragma unroll
+                    for (int u = 0; u < kLbUnroll; ++u) {
+                        const int j = C.ord[p + u];
+                        const bool okj = EAPDTW_CHECK(C.dbg, j >= 0 && j < m && i + j < C.ref.n, 23, j);
+                        const float uu = znorm1(okj ? __ldg(ur + j) : 0.0f, a, cw, isd);
+                        const float ll = znorm1(okj ? __ldg(lr + j) : 0.0f, a, cw, isd);
+                        const float qv = C.zqo[p + u];
+                        const float e = fmaxf(fmaxf(__fsub_rn(qv, uu), __fsub_rn(ll, qv)), 0.0f);
+                        s2 = __fmaf_rn(e, e, s2);
+                    }
+                    if (s2 > ub) break;
+                }
+                lb = fmaxf(lb, s2);
+                if (s2 > ub) {
+                    alive = false;
+                    why = 3;
+                }
+            }
+        }
+    }
+
+    if (!list_mode) {
+        const unsigned b1 = __ballot_sync(kFull, why == 1);
+        const unsigned b2 = __ballot_sync(kFull, why == 2);
+        const unsigned b3 = __ballot_sync(kFull, why == 3);
+        if (lane == 0) {
+            count(kCntWindows, nlanes);
+            count(kCntKim, __popc(b1));
+            count(kCntEq, __popc(b2));
+            count(kCntEc, __popc(b3));
+        }
+    }
+
+    // ---- EAPrunedDTW on the survivors, one warp per window ----------------
+    unsigned mask = __ballot_sync(kFull, alive);
+    while (mask) {
+        const int src = __ffs(mask) - 1;
+        mask &= mask - 1;
+        const float a_s = __shfl_sync(kFull, a, src);
+        const float cw_s = __shfl_sync(kFull, cw, src);
+        const float isd_s = __shfl_sync(kFull, isd, src);
+        const float lb_s = __shfl_sync(kFull, lb, src);
+        const int off = list_mode ? 0 : src;
+        const int64_t iw = i0 + off;
+        // ub steers warp-wide control flow (the recheck below skips the DTW
+        // for the whole warp): take lane 0's reading, because other warps
+        // lower the bound concurrently and lanes that load it at slightly
+        // different times may see different values.
+        float ub = __shfl_sync(kFull, C.bsf.load(), 0);
+#ifdef EAPDTW_DEVICE_CHECKS
+        EAPDTW_CHECK(C.dbg, __shfl_sync(kFull, __float_as_int(ub), 0) == __float_as_int(ub), 24, 0);
+        EAPDTW_CHECK(C.dbg, off >= 0 && off < 32 && iw < C.nw, 25, off);
+#endif
+        if (LB && C.use_lb && !list_mode && lb_s > ub * C.lb_scale) {
+            if (lane == 0) count(kCntRecheck, 1);
+            continue;
+        }
+        constexpr int kJ = WIDE ? 4 : dtw_windows(K, BAND);
+        const DtwOut o = dtw_warp<K, BAND, kJ, WIDE>(s_r + off, a_s, cw_s, isd_s, C.zq, m, m, C.w, C.bsf,
+                                                     ub, C.dbg);
+        if (lane == 0) {
+            count(kCntSteps, static_cast<unsigned long long>(o.steps));
+            count(kCntCells, static_cast<unsigned long long>(o.busy) * K);
+        }
+        if (o.status != 0) {
+            if (lane == 0) {
+                count(kCntOverflow, 1);
+                const int slot = atomicAdd(C.ovf_out_count, 1);
+                if (slot < C.ovf_cap) C.ovf_out[slot] = C.tag | static_cast<long long>(iw);
+            }
+            continue;
+        }
+        ub = __shfl_sync(kFull, C.bsf.load(), 0);
+        if (o.dist <= ub && o.dist < f_inf()) {
+            if (lane == 0) {
+                C.bsf.insert(o.dist, static_cast<uint32_t>(iw));
+                count(kCntCompleted, 1);
+            }
+        } else if (lane == 0) {
+            count(kCntAbandoned, 1);
+        }
+    }
+    __syncwarp();
 }
 
 // Resident blocks per SM the register allocation is sized for (registers per
@@ -112,166 +292,41 @@ search_kernel(const SearchArgs A) {
         const int c = *A.ovf_in_count;
         nitems = c < A.ovf_in_cap ? c : A.ovf_in_cap;
     }
-    const bool r_aligned = (reinterpret_cast<uintptr_t>(A.ref.R) & 15) == 0;
     auto count = [&](int c, unsigned long long v) { if (v) atomicAdd(s_cnt + c, v); };
+    TileCtx C;
+    C.ref = A.ref;
+    C.zq = s_zq;
+    C.uq = s_uq;
+    C.lq = s_lq;
+    C.zqo = s_zqo;
+    C.ord = s_ord;
+    C.m = m;
+    C.w = A.w;
+    C.use_lb = A.use_lb;
+    C.use_ec = A.use_lb;
+    C.ur = A.ur;
+    C.lr = A.lr;
+    C.lb_scale = A.lb_scale;
+    C.bsf = A.bsf;
+    C.nw = A.nw;
+    C.ovf_out = A.ovf_out;
+    C.ovf_out_count = A.ovf_out_count;
+    C.ovf_cap = A.ovf_cap;
+    C.tag = 0;
+    C.dbg = A.dbg;
 
     for (;;) {
         int item = 0;
         if (lane == 0) item = atomicAdd(A.work_counter, 1);
         item = __shfl_sync(kFull, item, 0);
         if (item >= nitems) break;
-
-        int64_t i0;
-        int nlanes;  // windows in this work item
         if (!list_mode) {
-            i0 = static_cast<int64_t>(item) * 32;
-            nlanes = static_cast<int>(A.nw - i0 < 32 ? A.nw - i0 : 32);
+            const int64_t i0 = static_cast<int64_t>(item) * 32;
+            process_tile<K, BAND, LB, WIDE>(C, s_r, false, i0, static_cast<int>(A.nw - i0 < 32 ? A.nw - i0 : 32),
+                                            count);
         } else {
-            i0 = A.ovf_in[item];
-            nlanes = 1;
+            process_tile<K, BAND, LB, WIDE>(C, s_r, true, A.ovf_in[item] & 0xffffffffll, 1, count);
         }
-        // Stage R[i0 .. i0 + nlanes - 1 + m) into the warp's tile.
-        const int len = nlanes - 1 + m;
-        if (!EAPDTW_CHECK(A.dbg, len <= tile_floats(m) && i0 >= 0 && i0 + len <= A.ref.n, 21, len)) break;
-        if (r_aligned && !list_mode) {
-            const float4* src = reinterpret_cast<const float4*>(A.ref.R + i0);
-            const int nv = len / 4;
-            for (int v = lane; v < nv; v += 32) reinterpret_cast<float4*>(s_r)[v] = __ldg(src + v);
-            for (int j = nv * 4 + lane; j < len; j += 32) s_r[j] = __ldg(A.ref.R + i0 + j);
-        } else {
-            for (int j = lane; j < len; j += 32) s_r[j] = __ldg(A.ref.R + i0 + j);
-        }
-        __syncwarp();
-
-        // ---- per-lane window statistics and lower bounds ------------------
-        const int my = list_mode ? 0 : lane;
-        const bool valid = lane < nlanes || list_mode;
-        const int64_t i = i0 + my;
-        float a = 0.0f, cw = 0.0f, isd = 0.0f;
-        if (valid) window_coeffs(A.ref, i, m, s_r + my, a, cw, isd);
-        float lb = 0.0f;
-        bool alive = valid && (!list_mode || lane == 0);
-        int why = 0;  // 1, 2, 3: pruned by LB_Kim, LB_Keogh EQ, LB_Keogh EC
-        if (LB && A.use_lb && alive && !list_mode) {
-            const float ub = A.bsf.load() * A.lb_scale;
-            const float* x = s_r + my;
-            const float z0 = znorm1(x[0], a, cw, isd);
-            const float d0 = __fsub_rn(z0, s_zq[0]);
-            float kim = __fmul_rn(d0, d0);
-            if (m > 1) {
-                const float dl = __fsub_rn(znorm1(x[m - 1], a, cw, isd), s_zq[m - 1]);
-                kim = __fmaf_rn(dl, dl, kim);
-            }
-            lb = kim;
-            if (kim > ub) {
-                alive = false;
-                why = 1;
-            } else {
-                // LB_Keogh EQ: the normalised window against the query envelope.
-                float s = 0.0f;
-                for (int p = 0; p < mp; p += kLbUnroll) {
-#pragma unroll
-                    for (int u = 0; u < kLbUnroll; ++u) {
-                        const int j = s_ord[p + u];
-                        const float z = znorm1(EAPDTW_CHECK(A.dbg, j >= 0 && j < m, 22, j) ? x[j] : 0.0f, a, cw, isd);
-                        const float e = fmaxf(fmaxf(__fsub_rn(z, s_uq[p + u]), __fsub_rn(s_lq[p + u], z)), 0.0f);
-                        s = __fmaf_rn(e, e, s);
-                    }
-                    if (s > ub) break;
-                }
-                lb = fmaxf(lb, s);
-                if (s > ub) {
-                    alive = false;
-                    why = 2;
-                } else {
-                    // LB_Keogh EC: the query against the window's envelope.
-                    float s2 = 0.0f;
-                    const float* ur = A.ur + i;
-                    const float* lr = A.lr + i;
-                    for (int p = 0; p < mp; p += kLbUnroll) {
-#pragma unroll
-                        for (int u = 0; u < kLbUnroll; ++u) {
-                            const int j = s_ord[p + u];
-                            const bool okj = EAPDTW_CHECK(A.dbg, j >= 0 && j < m && i + j < A.ref.n, 23, j);
-                            const float uu = znorm1(okj ? __ldg(ur + j) : 0.0f, a, cw, isd);
-                            const float ll = znorm1(okj ? __ldg(lr + j) : 0.0f, a, cw, isd);
-                            const float qv = s_zqo[p + u];
-                            const float e = fmaxf(fmaxf(__fsub_rn(qv, uu), __fsub_rn(ll, qv)), 0.0f);
-                            s2 = __fmaf_rn(e, e, s2);
-                        }
-                        if (s2 > ub) break;
-                    }
-                    lb = fmaxf(lb, s2);
-                    if (s2 > ub) {
-                        alive = false;
-                        why = 3;
-                    }
-                }
-            }
-        }
-
-        if (!list_mode) {
-            const unsigned b1 = __ballot_sync(kFull, why == 1);
-            const unsigned b2 = __ballot_sync(kFull, why == 2);
-            const unsigned b3 = __ballot_sync(kFull, why == 3);
-            if (lane == 0) {
-                count(kCntWindows, nlanes);
-                count(kCntKim, __popc(b1));
-                count(kCntEq, __popc(b2));
-                count(kCntEc, __popc(b3));
-            }
-        }
-
-        // ---- EAPrunedDTW on the survivors, one warp per window ------------
-        unsigned mask = __ballot_sync(kFull, alive);
-        while (mask) {
-            const int src = __ffs(mask) - 1;
-            mask &= mask - 1;
-            const float a_s = __shfl_sync(kFull, a, src);
-            const float cw_s = __shfl_sync(kFull, cw, src);
-            const float isd_s = __shfl_sync(kFull, isd, src);
-            const float lb_s = __shfl_sync(kFull, lb, src);
-            const int off = list_mode ? 0 : src;
-            const int64_t iw = i0 + off;
-            // ub steers warp-wide control flow (the recheck below skips the
-            // DTW for the whole warp): take lane 0's reading, because other
-            // warps lower the bound concurrently and lanes that load it at
-            // slightly different times may see different values.
-            float ub = __shfl_sync(kFull, A.bsf.load(), 0);
-#ifdef EAPDTW_DEVICE_CHECKS
-            EAPDTW_CHECK(A.dbg, __shfl_sync(kFull, __float_as_int(ub), 0) == __float_as_int(ub), 24, 0);
-            EAPDTW_CHECK(A.dbg, off >= 0 && off < 32 && iw < A.nw, 25, off);
-#endif
-            if (LB && A.use_lb && !list_mode && lb_s > ub * A.lb_scale) {
-                if (lane == 0) count(kCntRecheck, 1);
-                continue;
-            }
-            constexpr int kJ = WIDE ? 4 : dtw_windows(K, BAND);
-            const DtwOut o = dtw_warp<K, BAND, kJ, WIDE>(s_r + off, a_s, cw_s, isd_s, s_zq, m, m, A.w,
-                                                         A.bsf, ub, A.dbg);
-            if (lane == 0) {
-                count(kCntSteps, static_cast<unsigned long long>(o.steps));
-                count(kCntCells, static_cast<unsigned long long>(o.busy) * K);
-            }
-            if (o.status != 0) {
-                if (lane == 0) {
-                    count(kCntOverflow, 1);
-                    const int slot = atomicAdd(A.ovf_out_count, 1);
-                    if (slot < A.ovf_cap) A.ovf_out[slot] = static_cast<int>(iw);
-                }
-                continue;
-            }
-            ub = __shfl_sync(kFull, A.bsf.load(), 0);
-            if (o.dist <= ub && o.dist < f_inf()) {
-                if (lane == 0) {
-                    A.bsf.insert(o.dist, static_cast<uint32_t>(iw));
-                    count(kCntCompleted, 1);
-                }
-            } else if (lane == 0) {
-                count(kCntAbandoned, 1);
-            }
-        }
-        __syncwarp();
     }
 
     __syncthreads();
