@@ -186,6 +186,92 @@ int32_t eapdtw_release_scratch(void);
 int32_t subseq_search_noalloc(const float* Q, int64_t lQ, const float* R, int64_t lR, int64_t w,
                               int32_t k, int64_t* out_idx, double* out_dist, void* stream);
 
+/* ------------------------------------------------------------------------
+ * Contexts and the batched search.
+ *
+ * Not in the paper, which searches one query in one series at a time
+ * (Section 5): a context keeps references resident on one device (their raw
+ * values and the chunk-anchored FP64 prefix sums behind the window statistics)
+ * and runs many (query, reference) items in one launch sequence.  Each item is
+ * exactly a subseq_search(Q, lQ, R, lR, w, k) call and returns the same
+ * result (the lower bounds change which windows reach EAPrunedDTW, never the
+ * result; LB_Keogh EC is not used in batches).
+ * ------------------------------------------------------------------------ */
+typedef struct eapdtw_ctx eapdtw_ctx;
+
+/* One item of a batch. */
+typedef struct {
+    const float* Q;    /* DEVICE pointer to lQ query values (caller-owned; read during the call) */
+    int64_t lQ;        /* 1 <= lQ <= min(EAPDTW_MAX_QUERY, length of the reference) */
+    int64_t w;         /* warping window, >= 0 (w >= lQ - 1: unconstrained) */
+    int32_t ref_id;    /* a reference registered with the context */
+    int32_t k;         /* 1 <= k <= kstride of the call */
+    int32_t no_lb;     /* 1: skip LB_Kim / LB_Keogh for this item */
+    int32_t reserved;  /* set to 0 */
+} eapdtw_item;
+
+/* eapdtw_ctx_create - a context on CUDA device `device`.  mem_budget (bytes,
+ * 0 = no limit) bounds the device memory the context holds: resident
+ * references plus its batch arena; a call that would exceed it returns
+ * EAPDTW_ERR_OUT_OF_MEMORY and leaves the context unchanged. */
+int32_t eapdtw_ctx_create(int32_t device, int64_t mem_budget, eapdtw_ctx** out);
+
+/* eapdtw_ctx_destroy - wait for the device, free everything the context holds. */
+int32_t eapdtw_ctx_destroy(eapdtw_ctx* ctx);
+
+/* eapdtw_ref_register - COPY the device series R[0..lR) into the context and
+ * build its window statistics (chunk-anchored FP64 prefix sums, 20 bytes per
+ * point in all).  The caller may free R when the call returns (blocking).
+ * lR < 2^31.  A NaN or Inf in R returns EAPDTW_ERR_NAN_INPUT and registers
+ * nothing.  *ref_id receives the handle. */
+int32_t eapdtw_ref_register(eapdtw_ctx* ctx, const float* R, int64_t lR, int32_t* ref_id, void* stream);
+
+/* eapdtw_ref_unregister - wait for the device, then free a reference. */
+int32_t eapdtw_ref_unregister(eapdtw_ctx* ctx, int32_t ref_id);
+
+/* eapdtw_ref_info - device address and length of a registered reference's
+ * copy (owned by the context; valid until it is unregistered). */
+int32_t eapdtw_ref_info(eapdtw_ctx* ctx, int32_t ref_id, const float** R, int64_t* lR);
+
+/* eapdtw_ctx_info - out[0..min(nout, EAPDTW_CTX_NINFO)): bytes held, budget,
+ * live references, batch arena bytes, batches run, items run, items that were
+ * re-run alone (a re-run list was full), 1 if the launch graph is captured. */
+#define EAPDTW_CTX_NINFO 8
+int32_t eapdtw_ctx_info(eapdtw_ctx* ctx, int64_t* out, int32_t nout);
+
+/* eapdtw_search_batch - run n items (a HOST array) on the context's device.
+ * Item i's k results go to out_idx/out_dist[i*kstride .. i*kstride + k)
+ * (DEVICE arrays of n*kstride), ascending by (distance, index) as in
+ * subseq_search; slots k..kstride-1 hold (-1, +inf).  Items that share the
+ * same (Q pointer, lQ, w) share one query preparation.  counters: optional
+ * HOST int64[EAPDTW_NCOUNTERS] with the summed counters 0..9 of the batch.
+ * Blocking.  The launch sequence is captured into a CUDA graph on the first
+ * call (and again after the context's arena grows), so the call must not be
+ * made while `stream` is being captured.  kstride <= EAPDTW_MAX_K. */
+int32_t eapdtw_search_batch(eapdtw_ctx* ctx, const eapdtw_item* items, int32_t n, int32_t kstride,
+                            int64_t* out_idx, double* out_dist, int64_t* counters, void* stream);
+
+/* eapdtw_set_first_tile - the autotuner's choice of the first level's DP
+ * cells per lane (4, 8, 16, 32; 0 = the built-in rule) for items with
+ * floor(log2 lQ) == log2_m, window ratio floor(10 w / lQ) == ratio_tenths
+ * (10 for unconstrained) and band (0 unconstrained, 1 banded).  Any choice
+ * gives the same results; only the speed differs. */
+int32_t eapdtw_set_first_tile(eapdtw_ctx* ctx, int32_t log2_m, int32_t ratio_tenths, int32_t band, int32_t tile);
+
+/* eapdtw_get_first_tile - the table entry (0 = none, the built-in rule). */
+int32_t eapdtw_get_first_tile(eapdtw_ctx* ctx, int32_t log2_m, int32_t ratio_tenths, int32_t band, int32_t* tile);
+
+/* eapdtw_autotune - the autotuner of the first level's DP cells per lane.
+ * For every signature (see eapdtw_set_first_tile) of the n HOST items that
+ * has no table entry yet, it times the batched search of one representative
+ * item (the one with the longest reference) over a prefix of its reference
+ * holding about sample_windows windows, with the built-in choice, twice it
+ * and half it (two runs each, the faster counts, device time of the launch
+ * sequence), and enters the fastest.  *n_tuned (optional) receives the number
+ * of signatures entered.  Blocking; results of later searches are unchanged. */
+int32_t eapdtw_autotune(eapdtw_ctx* ctx, const eapdtw_item* items, int32_t n, int64_t sample_windows,
+                        void* stream, int32_t* n_tuned);
+
 #ifdef __cplusplus
 }
 #endif

@@ -9,6 +9,7 @@ step (build.py), the ctypes binding (api.py) and the seeded input generators
 (synth.py).
 """
 from .api import (  # noqa: F401
+    Context,
     EapDtwError,
     eap_dtw,
     eap_dtw_host,

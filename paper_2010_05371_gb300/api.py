@@ -39,6 +39,23 @@ class SearchOpts(C.Structure):
     ]
 
 
+class Item(C.Structure):
+    """eapdtw_item of include/eapdtw.h."""
+    _fields_ = [
+        ("Q", C.c_void_p),
+        ("lQ", C.c_int64),
+        ("w", C.c_int64),
+        ("ref_id", C.c_int32),
+        ("k", C.c_int32),
+        ("no_lb", C.c_int32),
+        ("reserved", C.c_int32),
+    ]
+
+
+CTX_INFO_NAMES = ("bytes_held", "budget", "live_refs", "arena_bytes", "batches", "items_run",
+                  "items_rerun", "graph_captured")
+
+
 class EapDtwError(RuntimeError):
     def __init__(self, code: int, what: str):
         super().__init__(f"{what}: {strerror(code)} ({code})")
@@ -76,6 +93,27 @@ def lib():
         L.eapdtw_release_scratch.argtypes = []
         L.subseq_search_noalloc.restype = i32
         L.subseq_search_noalloc.argtypes = [vp, i64, vp, i64, i64, i32, vp, vp, vp]
+        pi32 = C.POINTER(i32)
+        L.eapdtw_ctx_create.restype = i32
+        L.eapdtw_ctx_create.argtypes = [i32, i64, C.POINTER(vp)]
+        L.eapdtw_ctx_destroy.restype = i32
+        L.eapdtw_ctx_destroy.argtypes = [vp]
+        L.eapdtw_ref_register.restype = i32
+        L.eapdtw_ref_register.argtypes = [vp, vp, i64, pi32, vp]
+        L.eapdtw_ref_unregister.restype = i32
+        L.eapdtw_ref_unregister.argtypes = [vp, i32]
+        L.eapdtw_ref_info.restype = i32
+        L.eapdtw_ref_info.argtypes = [vp, i32, C.POINTER(vp), C.POINTER(i64)]
+        L.eapdtw_ctx_info.restype = i32
+        L.eapdtw_ctx_info.argtypes = [vp, C.POINTER(i64), i32]
+        L.eapdtw_search_batch.restype = i32
+        L.eapdtw_search_batch.argtypes = [vp, C.POINTER(Item), i32, i32, vp, vp, C.POINTER(i64), vp]
+        L.eapdtw_set_first_tile.restype = i32
+        L.eapdtw_set_first_tile.argtypes = [vp, i32, i32, i32, i32]
+        L.eapdtw_get_first_tile.restype = i32
+        L.eapdtw_get_first_tile.argtypes = [vp, i32, i32, i32, pi32]
+        L.eapdtw_autotune.restype = i32
+        L.eapdtw_autotune.argtypes = [vp, C.POINTER(Item), i32, i64, vp, pi32]
         _lib = L
     return _lib
 
@@ -213,3 +251,120 @@ def subseq_search_noalloc(Q, R, w: int, idx, dist, stream=None):
 
 def release_scratch():
     _check(lib().eapdtw_release_scratch(), "eapdtw_release_scratch")
+
+
+class Context:
+    """A context of include/eapdtw.h: references resident on one device and the
+    batched search over many (query, reference) items."""
+
+    def __init__(self, device: int = 0, mem_budget: int = 0):
+        h = C.c_void_p()
+        _check(lib().eapdtw_ctx_create(int(device), int(mem_budget), C.byref(h)), "eapdtw_ctx_create")
+        self._h = h
+        self.device = int(device)
+        self._refs = {}
+
+    def close(self):
+        if self._h is not None and self._h.value:
+            _check(lib().eapdtw_ctx_destroy(self._h), "eapdtw_ctx_destroy")
+        self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def register(self, R, stream=None) -> int:
+        """Copy the CUDA float32 series R into the context; returns its id."""
+        R = _dev_f32(R, "R")
+        rid = C.c_int32(-1)
+        _check(lib().eapdtw_ref_register(self._h, C.c_void_p(R.data_ptr()), R.numel(), C.byref(rid),
+                                         _stream_ptr(stream)), "eapdtw_ref_register")
+        self._refs[rid.value] = R.numel()
+        return rid.value
+
+    def unregister(self, ref_id: int):
+        _check(lib().eapdtw_ref_unregister(self._h, int(ref_id)), "eapdtw_ref_unregister")
+        self._refs.pop(int(ref_id), None)
+
+    def ref_length(self, ref_id: int) -> int:
+        n = C.c_int64(0)
+        _check(lib().eapdtw_ref_info(self._h, int(ref_id), None, C.byref(n)), "eapdtw_ref_info")
+        return n.value
+
+    def info(self) -> dict:
+        out = (C.c_int64 * len(CTX_INFO_NAMES))()
+        _check(lib().eapdtw_ctx_info(self._h, out, len(CTX_INFO_NAMES)), "eapdtw_ctx_info")
+        return dict(zip(CTX_INFO_NAMES, (int(v) for v in out)))
+
+    @staticmethod
+    def _items(items):
+        """items: sequence of (Q, ref_id, w, k) or (Q, ref_id, w, k, no_lb)."""
+        arr = (Item * len(items))()
+        keep = []
+        for i, t in enumerate(items):
+            Q = _dev_f32(t[0], "Q")
+            keep.append(Q)
+            arr[i].Q = Q.data_ptr()
+            arr[i].lQ = Q.numel()
+            arr[i].ref_id = int(t[1])
+            arr[i].w = int(t[2])
+            arr[i].k = int(t[3])
+            arr[i].no_lb = int(bool(t[4])) if len(t) > 4 else 0
+            arr[i].reserved = 0
+        return arr, keep
+
+    def search_batch(self, items, kstride: int | None = None, *, out=None, stream=None,
+                     return_counters: bool = False):
+        """Run every item; returns (idx int64[n, kstride], dist float64[n, kstride])
+        CUDA tensors (row i: item i's k results, then (-1, +inf)).  Blocking."""
+        import torch
+        n = len(items)
+        if n == 0:
+            raise ValueError("empty batch")
+        arr, keep = self._items(items)
+        if kstride is None:
+            kstride = max(int(t[3]) for t in items)
+        if out is None:
+            dev = torch.device("cuda", self.device)
+            idx = torch.empty((n, kstride), dtype=torch.int64, device=dev)
+            dist = torch.empty((n, kstride), dtype=torch.float64, device=dev)
+        else:
+            idx, dist = out
+        cnt = np.zeros(NCOUNTERS, dtype=np.int64)
+        rc = lib().eapdtw_search_batch(self._h, arr, n, int(kstride), C.c_void_p(idx.data_ptr()),
+                                       C.c_void_p(dist.data_ptr()), cnt.ctypes.data_as(C.POINTER(C.c_int64)),
+                                       _stream_ptr(stream))
+        del keep
+        _check(rc, "eapdtw_search_batch")
+        if return_counters:
+            return idx, dist, dict(zip(COUNTER_NAMES[:10], (int(c) for c in cnt[:10])))
+        return idx, dist
+
+    def autotune(self, items, sample_windows: int = 1 << 18, stream=None) -> int:
+        """Time the first-level tile choices for the items' signatures (see
+        eapdtw_autotune); returns the number of signatures entered."""
+        arr, keep = self._items(items)
+        nt = C.c_int32(0)
+        rc = lib().eapdtw_autotune(self._h, arr, len(items), int(sample_windows), _stream_ptr(stream),
+                                   C.byref(nt))
+        del keep
+        _check(rc, "eapdtw_autotune")
+        return nt.value
+
+    def set_first_tile(self, log2_m: int, ratio_tenths: int, band: int, tile: int):
+        _check(lib().eapdtw_set_first_tile(self._h, int(log2_m), int(ratio_tenths), int(band), int(tile)),
+               "eapdtw_set_first_tile")
+
+    def get_first_tile(self, log2_m: int, ratio_tenths: int, band: int) -> int:
+        t = C.c_int32(0)
+        _check(lib().eapdtw_get_first_tile(self._h, int(log2_m), int(ratio_tenths), int(band), C.byref(t)),
+               "eapdtw_get_first_tile")
+        return t.value

@@ -180,7 +180,6 @@ Scratch* scratch_for_current_device(int* dev_out) {
     return g_scratch[dev];
 }
 
-int32_t cuda_status(cudaError_t e) { return e == cudaSuccess ? EAPDTW_OK : EAPDTW_ERR_CUDA; }
 
 #define CK(expr)                                     \
     do {                                             \
@@ -227,7 +226,8 @@ int32_t search_impl(Scratch& S, const float* Q, int64_t lQ, const float* R, int6
             return EAPDTW_ERR_OUT_OF_MEMORY;
         S.cap_m = mp;
     }
-    const int want_ovf = static_cast<int>(nw < (1 << 22) ? nw : (1 << 22));
+    // a window overflows at most once per level: nw entries always suffice
+    const int want_ovf = static_cast<int>(nw);
     if (S.cap_ovf < want_ovf) {
         S.cap_ovf = 0;
         if (!alloc(S.ovf[0], want_ovf) || !alloc(S.ovf[1], want_ovf)) return EAPDTW_ERR_OUT_OF_MEMORY;

@@ -1,0 +1,191 @@
+// Device-side tables of a batched search: many (query, reference) items in
+// one launch sequence (eapdtw_search_batch).
+//
+// Work is cut into units that persistent warps take from one 64-bit counter
+// per launch:
+//  * seed units: the exact DTW of the sampled windows with the smallest
+//    z-normalised Euclidean distance (they seed each item's k-best list);
+//  * re-run units: single windows whose live region overflowed the warp's
+//    window of blocks at the previous (narrower) level;
+//  * tile units: 32 consecutive windows of one item, through the lower-bound
+//    cascade and EAPrunedDTW.
+// Items are grouped into classes by their first level (block width K) and
+// band mode; a class launch serves the seed and tile units of its items and
+// the re-run units its level receives.
+#pragma once
+
+#include <cstdint>
+
+#include "common.cuh"
+#include "search_kernel.cuh"
+
+namespace eapdtw {
+
+constexpr int kBatchLevels = 5;      // K = 4, 8, 16, 32, then the four-window level
+constexpr int kBatchClasses = 12;    // first levels 0..3 x band modes 0..2
+constexpr int kBatchSeedBest = 32;   // sampled windows per item run through exact DTW
+constexpr int kBatchSeedSamples = 4096;
+constexpr int kBatchSlots = 64;      // k-best slots per item (k <= 64)
+
+__host__ __device__ constexpr int batch_level_K(int level) { return level < 4 ? (4 << level) : 32; }
+
+struct BatchItem {
+    RefView ref;
+    const float* zq;     // query slot arrays (global memory; see TileCtx)
+    const float* uq;
+    const float* lq;
+    const float* zqo;
+    const int* ord;
+    int64_t nw;          // windows n - m + 1
+    int64_t seed_off;    // first sample of this item in the seed sample arrays
+    int m, w, k, use_lb;
+    int seed_ns;         // sampled windows (0: no seed)
+    int level0;          // first level
+    int band_next[kBatchLevels];  // band mode of the level that re-runs overflow from level L (-1: none)
+};
+
+struct BatchClass {
+    int item_off;   // citems[item_off .. item_off + nitems) are the items of the class
+    int nitems;
+    // cprefix[item_off + cls .. item_off + cls + nitems]: tile prefix over the class's items
+};
+
+struct QuerySlot {
+    const float* Q;  // raw query (caller's device memory)
+    int m, w;
+    int off;         // float offset of the slot's arrays in the query arena
+    int pad;
+};
+
+// Fixed device addresses of a context's batch arena.
+struct BatchDev {
+    const int* nitems;           // [1]
+    const int* nslots;           // [1]
+    const int* kstride;          // [1] result row length
+    const BatchItem* items;      // [cap_items]
+    const BatchClass* classes;   // [kBatchClasses]
+    const int* citems;           // [cap_items]
+    const int64_t* cprefix;      // [cap_items + kBatchClasses]
+    const int64_t* sprefix;      // [cap_items + 1] seed sample prefix
+    const QuerySlot* qslots;     // [cap_slots]
+    float* qarena;               // 5 arrays of mp floats per slot (ord stored as int)
+    int* qbad;                   // [cap_slots] non-finite query values
+    unsigned long long* slots;   // [cap_items * kBatchSlots]
+    float* ub_seed;              // [cap_items]
+    int* nbest;                  // [cap_items]
+    long long* best;             // [cap_items * kBatchSeedBest]
+    int* flags;                  // [cap_items] bit 0: an overflow entry was lost
+    float* seed_ed;              // [cap_samples]
+    int* seed_idx;               // [cap_samples]
+    int64_t* res_idx;            // [cap_items * kstride]
+    double* res_dist;
+};
+
+// One class launch of level `level` and band mode `band`.
+struct BatchLaunch {
+    BatchDev D;
+    int level;
+    int band;
+    int cls;                    // class of items whose first level this is (-1: none)
+    const long long* rr_in;     // re-run entries (item << 32 | window) for this level and band
+    const int* rr_in_count;
+    long long* rr_out;          // next level's lists: rr_out + b * rr_cap for band b
+    int* rr_out_count;          // [3]
+    int rr_cap;
+    unsigned long long* work;   // unit counter of this launch
+    unsigned long long* counters;
+    float lb_scale;
+};
+
+// Persistent batch kernel: the cascade and wavefront of process_tile, the
+// query and the windows read from global memory (items differ in length).
+template <int K, int BAND, bool WIDE>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32, WIDE ? 1 : search_min_blocks(K, BAND))
+batch_kernel(const BatchLaunch L) {
+    __shared__ unsigned long long s_cnt[kNumCounters];
+    if (threadIdx.x < kNumCounters) s_cnt[threadIdx.x] = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    int cn = 0, c0 = 0;
+    int64_t ntiles = 0;
+    const int64_t* P = nullptr;
+    if (L.cls >= 0) {
+        const BatchClass c = L.D.classes[L.cls];
+        cn = c.nitems;
+        c0 = c.item_off;
+        P = L.D.cprefix + c.item_off + L.cls;
+        ntiles = P[cn];
+    }
+    const int64_t nseed = static_cast<int64_t>(cn) * kBatchSeedBest;
+    int nrr = 0;
+    if (L.rr_in) {
+        const int c = *L.rr_in_count;
+        nrr = c < L.rr_cap ? c : L.rr_cap;
+    }
+    auto count = [&](int c, unsigned long long v) { if (v) atomicAdd(s_cnt + c, v); };
+    for (;;) {
+        unsigned long long u = 0;
+        if (lane == 0) u = atomicAdd(L.work, 1ull);
+        u = __shfl_sync(kFull, u, 0);
+        int item;
+        int64_t i0;
+        bool list;
+        int nl = 1;
+        const int64_t su = static_cast<int64_t>(u);
+        if (su < nseed) {
+            const int j = static_cast<int>(su / kBatchSeedBest);
+            const int s = static_cast<int>(su % kBatchSeedBest);
+            item = L.D.citems[c0 + j];
+            if (s >= L.D.nbest[item]) continue;
+            i0 = L.D.best[static_cast<int64_t>(item) * kBatchSeedBest + s] & 0xffffffffll;
+            list = true;
+        } else if (su < nseed + nrr) {
+            const long long e = L.rr_in[su - nseed];
+            item = static_cast<int>(e >> 32);
+            i0 = e & 0xffffffffll;
+            list = true;
+        } else {
+            const int64_t t = su - nseed - nrr;
+            if (t >= ntiles) break;
+            int lo = 0, hi = cn;  // P[lo] <= t < P[hi]
+            while (hi - lo > 1) {
+                const int mid = (lo + hi) >> 1;
+                if (P[mid] <= t) lo = mid;
+                else hi = mid;
+            }
+            item = L.D.citems[c0 + lo];
+            i0 = (t - P[lo]) * 32;
+            list = false;
+        }
+        const BatchItem& it = L.D.items[item];
+        if (!list) nl = static_cast<int>(it.nw - i0 < 32 ? it.nw - i0 : 32);
+        TileCtx C;
+        C.ref = it.ref;
+        C.zq = it.zq;
+        C.uq = it.uq;
+        C.lq = it.lq;
+        C.zqo = it.zqo;
+        C.ord = it.ord;
+        C.m = it.m;
+        C.w = it.w;
+        C.use_lb = it.use_lb;
+        C.use_ec = 0;
+        C.ur = nullptr;
+        C.lr = nullptr;
+        C.lb_scale = L.lb_scale;
+        C.bsf = BestSoFar{L.D.slots + static_cast<int64_t>(item) * kBatchSlots, L.D.ub_seed + item, it.k, 0, 0.0f};
+        C.nw = it.nw;
+        const int bn = it.band_next[L.level];
+        C.ovf_out = bn >= 0 ? L.rr_out + static_cast<int64_t>(bn) * L.rr_cap : nullptr;
+        C.ovf_out_count = bn >= 0 ? L.rr_out_count + bn : nullptr;
+        C.ovf_cap = bn >= 0 ? L.rr_cap : 0;
+        C.tag = static_cast<long long>(item) << 32;
+        C.lost = L.D.flags + item;
+        C.dbg = nullptr;
+        process_tile<K, BAND, !WIDE, WIDE, false>(C, nullptr, list, i0, nl, count);
+    }
+    __syncthreads();
+    if (threadIdx.x < 10 && s_cnt[threadIdx.x]) atomicAdd(L.counters + threadIdx.x, s_cnt[threadIdx.x]);
+}
+
+}  // namespace eapdtw

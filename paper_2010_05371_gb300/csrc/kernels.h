@@ -10,6 +10,8 @@
 namespace eapdtw {
 
 struct SearchArgs;
+struct BatchDev;
+struct BatchLaunch;
 
 cudaError_t launch_ref_prefix(const float* R, int64_t n, double* P1, double* P2, double* T1,
                               double* T2, float* A, int* bad, cudaStream_t s);
@@ -36,5 +38,20 @@ int search_blocks_wide(int band, int m);
 // eap_dtw single pair: one warp; wide selects the four-window level.
 cudaError_t launch_pair(int K, int band, bool wide, const float* rows, int nr, const float* cols, int nc,
                         int w, float ub, double* out, cudaStream_t s);
+
+// Batched search (batch.cuh): preparation (state reset, query slots, seed
+// samples and selection) and result conversion; query_prep shared memory is
+// sized for queries up to m_cap points (batch_prep_attributes sets it and must
+// run outside stream capture).
+cudaError_t batch_prep_attributes(int m_cap);
+cudaError_t launch_batch_prep(const BatchDev& D, int cap_items, unsigned long long* counters, int ncounters,
+                              unsigned long long* work, int nwork, int* rr_counts, int nrr, int m_cap,
+                              cudaStream_t s);
+cudaError_t launch_batch_finalize(const BatchDev& D, cudaStream_t s);
+// batch_kernel<K, BAND, WIDE> for one level (0..3: K = 4 << level; 4: the
+// four-window level); batch_attributes must run outside stream capture.
+cudaError_t launch_batch(int level, int band, const BatchLaunch& args, int blocks, cudaStream_t s);
+int batch_blocks(int level, int band);
+cudaError_t batch_attributes();
 
 }  // namespace eapdtw

@@ -7,6 +7,7 @@
 #include "common.cuh"
 #include "kernels.h"
 #include "search_kernel.cuh"
+#include "batch.cuh"
 
 namespace eapdtw {
 
@@ -78,10 +79,10 @@ __global__ void __launch_bounds__(256) ref_prefix_kernel(const float* __restrict
 // positions by decreasing |zq| (ties by position) used to visit LB terms.
 // Arrays are padded to query_pad(m) with neutral terms.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(1024) query_prep_kernel(const float* __restrict__ Q, int m, int w,
-                                                          float* zq, float* uq_o, float* lq_o,
-                                                          float* zq_o, int* ord, int* bad) {
-    extern __shared__ __align__(16) unsigned char sm[];
+// Body shared by the one-query kernel and the batch kernel (sm: dynamic
+// shared memory of query_prep_smem(m) bytes; all threads of the block call it).
+__device__ void query_prep_block(const float* __restrict__ Q, int m, int w, float* zq, float* uq_o,
+                                 float* lq_o, float* zq_o, int* ord, int* bad, unsigned char* sm) {
     const int tid = threadIdx.x;
     const int np2 = 1 << (32 - __clz(m - 1 > 0 ? m - 1 : 1));  // next pow2 >= m (>= 2)
     float* s_z = reinterpret_cast<float*>(sm);                // [m]
@@ -177,6 +178,14 @@ __global__ void __launch_bounds__(1024) query_prep_kernel(const float* __restric
             zq_o[p] = __int_as_float(0x7fffffff);
         }
     }
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(1024) query_prep_kernel(const float* __restrict__ Q, int m, int w,
+                                                          float* zq, float* uq_o, float* lq_o,
+                                                          float* zq_o, int* ord, int* bad) {
+    extern __shared__ __align__(16) unsigned char sm[];
+    query_prep_block(Q, m, w, zq, uq_o, lq_o, zq_o, ord, bad, sm);
 }
 
 size_t query_prep_smem(int m) {
@@ -271,11 +280,10 @@ __global__ void init_state_kernel(unsigned long long* slots, int k, float* ub_se
 // bounds the k-th smallest DTW from above (the sampled windows are real
 // candidates that the search will also visit).
 // ---------------------------------------------------------------------------
-__global__ void seed_ed_kernel(const RefView ref, const float* __restrict__ zq, int m, int64_t nw,
-                               int nsamples, float* ed, int* idx) {
+// Sample gw of nsamples (spread evenly over the nw windows) on one warp.
+__device__ __forceinline__ void seed_ed_sample(const RefView& ref, const float* __restrict__ zq, int m,
+                                              int64_t nw, int nsamples, int gw, float* ed, int* idx) {
     const int lane = threadIdx.x & 31;
-    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (gw >= nsamples) return;
     const int64_t i = nsamples > 1 ? (nw - 1) * gw / (nsamples - 1) : 0;
     const float* x = ref.R + i;
     double mean, var, m2a;
@@ -299,13 +307,21 @@ __global__ void seed_ed_kernel(const RefView ref, const float* __restrict__ zq, 
     }
 }
 
+__global__ void seed_ed_kernel(const RefView ref, const float* __restrict__ zq, int m, int64_t nw,
+                               int nsamples, float* ed, int* idx) {
+    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (gw >= nsamples) return;
+    seed_ed_sample(ref, zq, m, nw, nsamples, gw, ed, idx);
+}
+
 // One block: ub_seed = the k-th smallest sampled ED (distinct windows; +inf if
 // fewer than k are finite), raised by 0.1% so that FP32 rounding of the ED sum
 // cannot place it below the DTW of its own window; also writes the windows of
 // the `nbest` smallest samples (for an exact DTW pass that seeds the k-best list).
-__global__ void __launch_bounds__(1024) seed_select_kernel(const float* ed, const int* idx, int ns, int k,
-                                                           float* ub_seed, long long* best, int nbest,
-                                                           int* nbest_out) {
+// Body shared by the one-query and batch kernels (all threads of the block
+// call it; best entries are tag | window).
+__device__ void seed_select_block(const float* ed, const int* idx, int ns, int k, float* ub_seed,
+                                  long long* best, int nbest, int* nbest_out, long long tag) {
     __shared__ float s_v[64];
     __shared__ int s_i[64];
     __shared__ float r_v[32];
@@ -346,9 +362,16 @@ __global__ void __launch_bounds__(1024) seed_select_kernel(const float* ed, cons
         const float kth = taken >= k ? s_v[k - 1] : INF;
         *ub_seed = kth < INF ? kth * 1.001f : INF;
         int nb = 0;
-        for (int q = 0; q < taken && q < nbest; ++q) best[nb++] = idx[s_i[q]];
+        for (int q = 0; q < taken && q < nbest; ++q) best[nb++] = tag | static_cast<long long>(idx[s_i[q]]);
         *nbest_out = nb;
     }
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(1024) seed_select_kernel(const float* ed, const int* idx, int ns, int k,
+                                                           float* ub_seed, long long* best, int nbest,
+                                                           int* nbest_out) {
+    seed_select_block(ed, idx, ns, k, ub_seed, best, nbest, nbest_out, 0);
 }
 
 // ---------------------------------------------------------------------------
@@ -364,6 +387,89 @@ __global__ void finalize_kernel(const unsigned long long* slots, int k, int64_t*
         } else {
             out_idx[j] = static_cast<int64_t>(key & 0xffffffffull);
             out_dist[j] = static_cast<double>(__uint_as_float(static_cast<uint32_t>(key >> 32)));
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Batch versions (fixed grids that loop over the items and query slots named
+// in the device tables, so that one captured graph serves every batch).
+// ---------------------------------------------------------------------------
+__global__ void batch_init_kernel(BatchDev D, int cap_items, unsigned long long* counters, int ncounters,
+                                  unsigned long long* work, int nwork, int* rr_counts, int nrr) {
+    const int n = *D.nitems;
+    const int64_t tid = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+    for (int64_t j = tid; j < static_cast<int64_t>(n) * kBatchSlots; j += stride) D.slots[j] = kEmptyKey;
+    for (int64_t j = tid; j < n; j += stride) {
+        D.ub_seed[j] = __int_as_float(0x7f800000);
+        D.nbest[j] = 0;
+        D.flags[j] = 0;
+    }
+    for (int64_t j = tid; j < *D.nslots; j += stride) D.qbad[j] = 0;
+    if (tid < ncounters) counters[tid] = 0;
+    if (tid < nwork) work[tid] = 0;
+    if (tid < nrr) rr_counts[tid] = 0;
+    (void)cap_items;
+}
+
+__global__ void __launch_bounds__(1024) batch_query_prep_kernel(BatchDev D, int mp_cap) {
+    extern __shared__ __align__(16) unsigned char sm[];
+    const int ns = *D.nslots;
+    for (int q = blockIdx.x; q < ns; q += gridDim.x) {
+        const QuerySlot S = D.qslots[q];
+        const int mp = query_pad(S.m);
+        float* base = D.qarena + S.off;
+        query_prep_block(S.Q, S.m, S.w, base, base + mp, base + 2 * mp, base + 3 * mp,
+                         reinterpret_cast<int*>(base + 4 * mp), D.qbad + q, sm);
+    }
+    (void)mp_cap;
+}
+
+// One warp per sample; sample g belongs to the item whose prefix range holds it.
+__global__ void batch_seed_ed_kernel(BatchDev D) {
+    const int n = *D.nitems;
+    const int64_t total = D.sprefix[n];
+    const int64_t warps = (static_cast<int64_t>(gridDim.x) * blockDim.x) >> 5;
+    for (int64_t g = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; g < total; g += warps) {
+        int lo = 0, hi = n;  // sprefix[lo] <= g < sprefix[hi]
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (D.sprefix[mid] <= g) lo = mid;
+            else hi = mid;
+        }
+        const BatchItem& it = D.items[lo];
+        const int s = static_cast<int>(g - D.sprefix[lo]);
+        seed_ed_sample(it.ref, it.zq, it.m, it.nw, it.seed_ns, s, D.seed_ed + it.seed_off, D.seed_idx + it.seed_off);
+    }
+}
+
+__global__ void __launch_bounds__(1024) batch_seed_select_kernel(BatchDev D) {
+    const int n = *D.nitems;
+    for (int i = blockIdx.x; i < n; i += gridDim.x) {
+        const BatchItem& it = D.items[i];
+        if (it.seed_ns <= 0) continue;  // uniform over the block
+        seed_select_block(D.seed_ed + it.seed_off, D.seed_idx + it.seed_off, it.seed_ns, it.k, D.ub_seed + i,
+                          D.best + static_cast<int64_t>(i) * kBatchSeedBest, kBatchSeedBest, D.nbest + i,
+                          static_cast<long long>(i) << 32);
+    }
+}
+
+__global__ void batch_finalize_kernel(BatchDev D) {
+    const int n = *D.nitems;
+    const int ks = *D.kstride;
+    const int64_t total = static_cast<int64_t>(n) * ks;
+    for (int64_t g = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; g < total;
+         g += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const int i = static_cast<int>(g / ks);
+        const int j = static_cast<int>(g % ks);
+        const unsigned long long key = j < D.items[i].k ? D.slots[static_cast<int64_t>(i) * kBatchSlots + j] : kEmptyKey;
+        if (key == kEmptyKey) {
+            D.res_idx[g] = -1;
+            D.res_dist[g] = __longlong_as_double(0x7ff0000000000000ll);
+        } else {
+            D.res_idx[g] = static_cast<int64_t>(key & 0xffffffffull);
+            D.res_dist[g] = static_cast<double>(__uint_as_float(static_cast<uint32_t>(key >> 32)));
         }
     }
 }
@@ -418,6 +524,39 @@ cudaError_t launch_seed(const RefView& ref, const float* zq, int m, int64_t nw, 
 cudaError_t launch_finalize(const unsigned long long* slots, int k, int64_t* out_idx,
                             double* out_dist, cudaStream_t s) {
     finalize_kernel<<<1, 64, 0, s>>>(slots, k, out_idx, out_dist);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_prep(const BatchDev& D, int cap_items, unsigned long long* counters, int ncounters,
+                              unsigned long long* work, int nwork, int* rr_counts, int nrr, int m_cap,
+                              cudaStream_t s) {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    batch_init_kernel<<<sms * 4, 256, 0, s>>>(D, cap_items, counters, ncounters, work, nwork, rr_counts, nrr);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const size_t sm = query_prep_smem(m_cap);
+    batch_query_prep_kernel<<<sms, 1024, sm, s>>>(D, query_pad(m_cap));
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    batch_seed_ed_kernel<<<sms * 8, 256, 0, s>>>(D);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    batch_seed_select_kernel<<<sms, 1024, 0, s>>>(D);
+    return cudaGetLastError();
+}
+
+cudaError_t batch_prep_attributes(int m_cap) {
+    return cudaFuncSetAttribute(batch_query_prep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                static_cast<int>(query_prep_smem(m_cap)));
+}
+
+cudaError_t launch_batch_finalize(const BatchDev& D, cudaStream_t s) {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    batch_finalize_kernel<<<sms, 256, 0, s>>>(D);
     return cudaGetLastError();
 }
 

@@ -88,31 +88,40 @@ struct TileCtx {
     int* ovf_out_count;
     int ovf_cap;
     long long tag;        // high bits of the overflow entries (batch item << 32)
+    int* lost;            // set to 1 when an overflow entry did not fit the list (or nullptr)
     int* dbg;
 };
 
 // One work item on one warp: a tile of nlanes (<= 32) consecutive windows
-// starting at i0, or (list_mode) the single window i0.  Stages the windows'
-// points into the warp's shared-memory tile s_r, runs the lower bounds lane by
-// lane (tile mode), then EAPrunedDTW for every survivor on the whole warp.
-template <int K, int BAND, bool LB, bool WIDE, typename CountF>
+// starting at i0, or (list_mode) the single window i0.  STAGE: copy the
+// windows' points into the warp's shared-memory tile s_r first (one query per
+// launch); otherwise read them from the reference in global memory through L1
+// (a batch, whose query lengths differ from item to item).  Then the lower
+// bounds lane by lane (tile mode), then EAPrunedDTW for every survivor on the
+// whole warp.
+template <int K, int BAND, bool LB, bool WIDE, bool STAGE = true, typename CountF>
 __device__ __forceinline__ void process_tile(const TileCtx& C, float* s_r, bool list_mode, int64_t i0,
                                              int nlanes, CountF count) {
     const int lane = threadIdx.x & 31;
     const int m = C.m;
     const int mp = query_pad(m);
-    // Stage R[i0 .. i0 + nlanes - 1 + m) into the warp's tile.
     const int len = nlanes - 1 + m;
-    if (!EAPDTW_CHECK(C.dbg, len <= tile_floats(m) && i0 >= 0 && i0 + len <= C.ref.n, 21, len)) return;
-    if ((reinterpret_cast<uintptr_t>(C.ref.R + i0) & 15) == 0 && !list_mode) {
-        const float4* src = reinterpret_cast<const float4*>(C.ref.R + i0);
-        const int nv = len / 4;
-        for (int v = lane; v < nv; v += 32) reinterpret_cast<float4*>(s_r)[v] = __ldg(src + v);
-        for (int j = nv * 4 + lane; j < len; j += 32) s_r[j] = __ldg(C.ref.R + i0 + j);
+    if (!EAPDTW_CHECK(C.dbg, i0 >= 0 && i0 + len <= C.ref.n, 21, len)) return;
+    if (STAGE) {
+        // R[i0 .. i0 + nlanes - 1 + m) into the warp's tile.
+        if (!EAPDTW_CHECK(C.dbg, len <= tile_floats(m), 26, len)) return;
+        if ((reinterpret_cast<uintptr_t>(C.ref.R + i0) & 15) == 0 && !list_mode) {
+            const float4* src = reinterpret_cast<const float4*>(C.ref.R + i0);
+            const int nv = len / 4;
+            for (int v = lane; v < nv; v += 32) reinterpret_cast<float4*>(s_r)[v] = __ldg(src + v);
+            for (int j = nv * 4 + lane; j < len; j += 32) s_r[j] = __ldg(C.ref.R + i0 + j);
+        } else {
+            for (int j = lane; j < len; j += 32) s_r[j] = __ldg(C.ref.R + i0 + j);
+        }
+        __syncwarp();
     } else {
-        for (int j = lane; j < len; j += 32) s_r[j] = __ldg(C.ref.R + i0 + j);
+        s_r = const_cast<float*>(C.ref.R + i0);
     }
-    __syncwarp();
 
     // ---- per-lane window statistics and lower bounds ----------------------
     const int my = list_mode ? 0 : lane;
@@ -227,8 +236,9 @@ __device__ __forceinline__ void process_tile(const TileCtx& C, float* s_r, bool 
         if (o.status != 0) {
             if (lane == 0) {
                 count(kCntOverflow, 1);
-                const int slot = atomicAdd(C.ovf_out_count, 1);
+                const int slot = C.ovf_out_count ? atomicAdd(C.ovf_out_count, 1) : C.ovf_cap;
                 if (slot < C.ovf_cap) C.ovf_out[slot] = C.tag | static_cast<long long>(iw);
+                else if (C.lost) atomicOr(C.lost, 1);
             }
             continue;
         }
@@ -313,6 +323,7 @@ search_kernel(const SearchArgs A) {
     C.ovf_out_count = A.ovf_out_count;
     C.ovf_cap = A.ovf_cap;
     C.tag = 0;
+    C.lost = nullptr;
     C.dbg = A.dbg;
 
     for (;;) {

@@ -50,3 +50,19 @@ def test_argument_errors_need_no_gpu(libpath):
     # beyond this build's limits
     assert L.subseq_search(buf, 5000, buf, 6000, 1, 1, i64, f64, None) == -6
     assert L.subseq_search(buf, 4, buf, 8, 1, 65, i64, f64, None) == -6
+
+
+def test_context_argument_errors_need_no_gpu(libpath):
+    """The context and batch entry points reject invalid arguments before any CUDA call."""
+    L = api.lib()
+    assert L.eapdtw_ctx_create(0, 0, None) == -1
+    assert L.eapdtw_ctx_create(0, -5, ctypes.byref(ctypes.c_void_p())) == -1
+    assert L.eapdtw_ctx_destroy(None) == -1
+    assert L.eapdtw_ref_register(None, None, 10, None, None) == -1
+    assert L.eapdtw_ref_unregister(None, 0) == -1
+    assert L.eapdtw_search_batch(None, None, 1, 1, None, None, None, None) == -1
+    assert L.eapdtw_autotune(None, None, 1, 1000, None, None) == -1
+    assert L.eapdtw_set_first_tile(None, 5, 1, 1, 8) == -1
+    assert L.eapdtw_ctx_info(None, None, 1) == -1
+    # the item struct of the binding has the header's layout
+    assert ctypes.sizeof(api.Item) == 40
