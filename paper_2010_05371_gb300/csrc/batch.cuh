@@ -42,6 +42,9 @@ struct BatchItem {
     int seed_ns;         // sampled windows (0: no seed)
     int level0;          // first level
     int band_next[kBatchLevels];  // band mode of the level that re-runs overflow from level L (-1: none)
+    const float* eu;     // sparse-table level of the reference for LB_Keogh EC (see TileCtx)
+    const float* el;
+    int ec_w, ec_d;
 };
 
 struct BatchClass {
@@ -169,9 +172,13 @@ batch_kernel(const BatchLaunch L) {
         C.m = it.m;
         C.w = it.w;
         C.use_lb = it.use_lb;
-        C.use_ec = 0;
+        C.use_ec = it.use_lb;
         C.ur = nullptr;
         C.lr = nullptr;
+        C.eu = it.eu;
+        C.el = it.el;
+        C.ec_w = it.ec_w;
+        C.ec_d = it.ec_d;
         C.lb_scale = L.lb_scale;
         C.bsf = BestSoFar{L.D.slots + static_cast<int64_t>(item) * kBatchSlots, L.D.ub_seed + item, it.k, 0, 0.0f};
         C.nw = it.nw;
@@ -182,7 +189,7 @@ batch_kernel(const BatchLaunch L) {
         C.tag = static_cast<long long>(item) << 32;
         C.lost = L.D.flags + item;
         C.dbg = nullptr;
-        process_tile<K, BAND, !WIDE, WIDE, false>(C, nullptr, list, i0, nl, count);
+        process_tile<K, BAND, !WIDE, WIDE, false, 2>(C, nullptr, list, i0, nl, count);
     }
     __syncthreads();
     if (threadIdx.x < 10 && s_cnt[threadIdx.x]) atomicAdd(L.counters + threadIdx.x, s_cnt[threadIdx.x]);

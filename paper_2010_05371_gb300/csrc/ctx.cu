@@ -29,6 +29,8 @@ constexpr int kNumWork = kBatchLevels * 3;
 
 int64_t al256(int64_t x) { return (x + 255) / 256 * 256; }
 
+constexpr int kEnvLevels = 13;   // running extrema over 2^p points, p = 0..12 (radius <= 4095)
+
 struct RefEntry {
     bool live = false;
     float* R = nullptr;
@@ -36,7 +38,33 @@ struct RefEntry {
     double *P1 = nullptr, *P2 = nullptr, *T1 = nullptr, *T2 = nullptr;
     float* A = nullptr;
     int64_t bytes = 0;
+    // sparse table of running maxima / minima for LB_Keogh EC, built on demand;
+    // level 0 is R itself
+    float* emax[kEnvLevels] = {nullptr};
+    float* emin[kEnvLevels] = {nullptr};
+    int env_levels = 1;
 };
+
+void free_ref(RefEntry& r) {
+    for (int p = 1; p < kEnvLevels; ++p) {
+        if (r.emax[p]) cudaFree(r.emax[p]);
+        if (r.emin[p]) cudaFree(r.emin[p]);
+    }
+    if (r.R) cudaFree(r.R);
+    if (r.P1) cudaFree(r.P1);
+    if (r.P2) cudaFree(r.P2);
+    if (r.T1) cudaFree(r.T1);
+    if (r.T2) cudaFree(r.T2);
+    if (r.A) cudaFree(r.A);
+    r = RefEntry{};
+}
+
+// Level of the table for envelope radius r: the largest p with 2^p <= 2r + 1.
+int env_level(int r) {
+    int p = 0;
+    while ((2 << p) <= 2 * r + 1) ++p;
+    return p;
+}
 
 // Byte offsets of the work tables (the same layout on the host staging buffer
 // and on the device).
@@ -382,9 +410,7 @@ int32_t eapdtw_ctx_destroy(eapdtw_ctx* c) {
         free_arena(c);
         if (c->ev0) cudaEventDestroy(c->ev0);
         if (c->ev1) cudaEventDestroy(c->ev1);
-        for (RefEntry& r : c->refs) {
-            dfree(r.R); dfree(r.P1); dfree(r.P2); dfree(r.T1); dfree(r.T2); dfree(r.A);
-        }
+        for (RefEntry& r : c->refs) free_ref(r);
         c->refs.clear();
         if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     }
@@ -426,6 +452,8 @@ int32_t eapdtw_ref_register(eapdtw_ctx* c, const float* R, int64_t lR, int32_t* 
     if (hbad) return undo(EAPDTW_ERR_NAN_INPUT);
     r.live = true;
     r.bytes = bytes;
+    r.emax[0] = r.R;
+    r.emin[0] = r.R;
     c->used += bytes;
     int id = -1;
     for (size_t i = 0; i < c->refs.size(); ++i)
@@ -448,9 +476,8 @@ int32_t eapdtw_ref_unregister(eapdtw_ctx* c, int32_t ref_id) {
     DeviceGuard g(c->device);
     cudaDeviceSynchronize();  // no batch may still read it
     RefEntry& r = c->refs[ref_id];
-    dfree(r.R); dfree(r.P1); dfree(r.P2); dfree(r.T1); dfree(r.T2); dfree(r.A);
     c->used -= r.bytes;
-    r = RefEntry{};
+    free_ref(r);
     return EAPDTW_OK;
 }
 
@@ -489,6 +516,31 @@ int32_t eapdtw_set_first_tile(eapdtw_ctx* c, int32_t log2_m, int32_t ratio_tenth
 }  // extern "C"
 
 namespace {
+
+// Build the reference's running-extrema table up to level p (blocking).
+int32_t ensure_env(eapdtw_ctx* c, RefEntry& r, int p, cudaStream_t st) {
+    if (p < r.env_levels) return EAPDTW_OK;
+    for (int q = r.env_levels; q <= p; ++q) {
+        int64_t bytes = 0;
+        if (!dalloc(r.emax[q], r.n, bytes) || !dalloc(r.emin[q], r.n, bytes) ||
+            (c->budget > 0 && c->used + bytes > c->budget)) {
+            dfree(r.emax[q]);
+            dfree(r.emin[q]);
+            return EAPDTW_ERR_OUT_OF_MEMORY;
+        }
+        if (launch_env_level(r.emax[q - 1], r.emin[q - 1], r.n, int64_t(1) << (q - 1), r.emax[q], r.emin[q], st) !=
+            cudaSuccess) {
+            cudaGetLastError();
+            dfree(r.emax[q]);
+            dfree(r.emin[q]);
+            return EAPDTW_ERR_CUDA;
+        }
+        c->used += bytes;
+        r.bytes += bytes;
+        r.env_levels = q + 1;
+    }
+    return EAPDTW_OK;
+}
 
 // The batched search with the context locked and its device current.
 // ref_len (optional): item i searches only the first ref_len[i] points of its
@@ -547,6 +599,12 @@ int32_t run_batch(eapdtw_ctx* c, const eapdtw_item* items, int32_t n, int32_t ks
         sum_nw += p.nw;
     }
     const int nslots = static_cast<int>(slots.size());
+    // running-extrema levels the items' LB_Keogh EC needs
+    for (int i = 0; i < n; ++i) {
+        if (items[i].no_lb) continue;
+        const int32_t e = ensure_env(c, c->refs[items[i].ref_id], env_level(std::min(P[i].w, P[i].m - 1)), st);
+        if (e != EAPDTW_OK) return e;
+    }
     int32_t rc = ensure_arena(c, n, nslots, qf, samples, sum_nw + static_cast<int64_t>(kBatchSeedBest) * n);
     if (rc != EAPDTW_OK) return rc;
 
@@ -600,6 +658,12 @@ int32_t run_batch(eapdtw_ctx* c, const eapdtw_item* items, int32_t n, int32_t ks
             else if (lv == 3 && p.m > 32 * 32) nxt = band_mode(4, p.w, p.unc);
             b.band_next[lv] = nxt;
         }
+        const int er = std::min(p.w, p.m - 1);
+        const int ep = env_level(er);
+        b.ec_w = er;
+        b.ec_d = er - (1 << ep) + 1;
+        b.eu = it.no_lb ? nullptr : r.emax[ep];
+        b.el = it.no_lb ? nullptr : r.emin[ep];
         hit[i] = b;
         sprefix[i + 1] = sprefix[i] + p.ns;
         BatchClass& k = cls[p.cls];

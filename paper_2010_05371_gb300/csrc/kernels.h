@@ -44,6 +44,9 @@ cudaError_t launch_pair(int K, int band, bool wide, const float* rows, int nr, c
 // sized for queries up to m_cap points (batch_prep_attributes sets it and must
 // run outside stream capture).
 cudaError_t batch_prep_attributes(int m_cap);
+// Level p of the running-extrema table from level p-1 (half = 2^(p-1)).
+cudaError_t launch_env_level(const float* smax, const float* smin, int64_t n, int64_t half, float* dmax,
+                             float* dmin, cudaStream_t s);
 cudaError_t launch_batch_prep(const BatchDev& D, int cap_items, unsigned long long* counters, int ncounters,
                               unsigned long long* work, int nwork, int* rr_counts, int nrr, int m_cap,
                               cudaStream_t s);

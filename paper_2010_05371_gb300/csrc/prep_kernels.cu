@@ -263,6 +263,21 @@ size_t envelope_smem(int w) { return sizeof(float) * 2 * (kEnvTile + 2 * static_
 int envelope_blocks(int64_t n) { return static_cast<int>((n + kEnvTile - 1) / kEnvTile); }
 
 // ---------------------------------------------------------------------------
+// Sparse table of running extrema (LB_Keogh EC of the batched search): level
+// p holds max / min of R[t .. min(t + 2^p, n)); level p comes from level p-1 as
+// the extremum of two runs of 2^(p-1) values.
+// ---------------------------------------------------------------------------
+__global__ void env_level_kernel(const float* __restrict__ smax, const float* __restrict__ smin, int64_t n,
+                                 int64_t half, float* dmax, float* dmin) {
+    for (int64_t t = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; t < n;
+         t += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const int64_t u = t + half < n ? t + half : t;
+        dmax[t] = fmaxf(smax[t], smax[u]);
+        dmin[t] = fminf(smin[t], smin[u]);
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Search state initialisation.
 // ---------------------------------------------------------------------------
 __global__ void init_state_kernel(unsigned long long* slots, int k, float* ub_seed,
@@ -544,6 +559,15 @@ cudaError_t launch_batch_prep(const BatchDev& D, int cap_items, unsigned long lo
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     batch_seed_select_kernel<<<sms, 1024, 0, s>>>(D);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_env_level(const float* smax, const float* smin, int64_t n, int64_t half, float* dmax,
+                             float* dmin, cudaStream_t s) {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    env_level_kernel<<<sms * 8, 256, 0, s>>>(smax, smin, n, half, dmax, dmin);
     return cudaGetLastError();
 }
 

@@ -78,9 +78,13 @@ struct TileCtx {
     int m;
     int w;
     int use_lb;           // LB_Kim and LB_Keogh EQ
-    int use_ec;           // LB_Keogh EC (needs ur / lr)
-    const float* ur;
+    int use_ec;           // LB_Keogh EC
+    const float* ur;      // envelope arrays U[t], L[t] of R over +-w (ECM = 1)
     const float* lr;
+    const float* eu;      // sparse-table level of running maxima / minima (ECM = 2): eu[t] =
+    const float* el;      // max R[t .. t + 2^p), clipped at the end; U[t] = max(eu[t - ec_w], eu[t + ec_d])
+    int ec_w;             // envelope radius
+    int ec_d;             // ec_w - 2^p + 1, with 2^p <= 2 ec_w + 1 < 2^(p+1)
     float lb_scale;
     BestSoFar bsf;
     int64_t nw;
@@ -99,7 +103,11 @@ struct TileCtx {
 // (a batch, whose query lengths differ from item to item).  Then the lower
 // bounds lane by lane (tile mode), then EAPrunedDTW for every survivor on the
 // whole warp.
-template <int K, int BAND, bool LB, bool WIDE, bool STAGE = true, typename CountF>
+// ECM: where LB_Keogh EC reads the reference envelope: 1 = arrays over the
+// window's own radius; 2 = a sparse table of running maxima / minima (any
+// radius, two reads per bound; windows within the radius of either end of the
+// reference use a slightly wider envelope, which is still a valid bound).
+template <int K, int BAND, bool LB, bool WIDE, bool STAGE = true, int ECM = 1, typename CountF>
 __device__ __forceinline__ void process_tile(const TileCtx& C, float* s_r, bool list_mode, int64_t i0,
                                              int nlanes, CountF count) {
     const int lane = threadIdx.x & 31;
@@ -166,20 +174,42 @@ __device__ __forceinline__ void process_tile(const TileCtx& C, float* s_r, bool 
             } else if (C.use_ec) {
                 // LB_Keogh EC: the query against the window's envelope.
                 float s2 = 0.0f;
-                const float* ur = C.ur + i;
-                const float* lr = C.lr + i;
-                for (int p = 0; p < mp; p += kLbUnroll) {
+                if (ECM == 1) {
+                    const float* ur = C.ur + i;
+                    const float* lr = C.lr + i;
+                    for (int p = 0; p < mp; p += kLbUnroll) {
 #pragma unroll
-                    for (int u = 0; u < kLbUnroll; ++u) {
-                        const int j = C.ord[p + u];
-                        const bool okj = EAPDTW_CHECK(C.dbg, j >= 0 && j < m && i + j < C.ref.n, 23, j);
-                        const float uu = znorm1(okj ? __ldg(ur + j) : 0.0f, a, cw, isd);
-                        const float ll = znorm1(okj ? __ldg(lr + j) : 0.0f, a, cw, isd);
-                        const float qv = C.zqo[p + u];
-                        const float e = fmaxf(fmaxf(__fsub_rn(qv, uu), __fsub_rn(ll, qv)), 0.0f);
-                        s2 = __fmaf_rn(e, e, s2);
+                        for (int u = 0; u < kLbUnroll; ++u) {
+                            const int j = C.ord[p + u];
+                            const bool okj = EAPDTW_CHECK(C.dbg, j >= 0 && j < m && i + j < C.ref.n, 23, j);
+                            const float uu = znorm1(okj ? __ldg(ur + j) : 0.0f, a, cw, isd);
+                            const float ll = znorm1(okj ? __ldg(lr + j) : 0.0f, a, cw, isd);
+                            const float qv = C.zqo[p + u];
+                            const float e = fmaxf(fmaxf(__fsub_rn(qv, uu), __fsub_rn(ll, qv)), 0.0f);
+                            s2 = __fmaf_rn(e, e, s2);
+                        }
+                        if (s2 > ub) break;
                     }
-                    if (s2 > ub) break;
+                } else {
+                    const int64_t nlast = C.ref.n - 1;
+                    const bool interior = i - C.ec_w >= 0 && i + (m - 1) + C.ec_w <= nlast;
+                    for (int p = 0; p < mp; p += kLbUnroll) {
+#pragma unroll
+                        for (int u = 0; u < kLbUnroll; ++u) {
+                            const int j = C.ord[p + u];
+                            int64_t x1 = i + j - C.ec_w, x2 = i + j + C.ec_d;
+                            if (!interior) {
+                                x1 = x1 < 0 ? 0 : (x1 > nlast ? nlast : x1);
+                                x2 = x2 < 0 ? 0 : (x2 > nlast ? nlast : x2);
+                            }
+                            const float uu = znorm1(fmaxf(__ldg(C.eu + x1), __ldg(C.eu + x2)), a, cw, isd);
+                            const float ll = znorm1(fminf(__ldg(C.el + x1), __ldg(C.el + x2)), a, cw, isd);
+                            const float qv = C.zqo[p + u];
+                            const float e = fmaxf(fmaxf(__fsub_rn(qv, uu), __fsub_rn(ll, qv)), 0.0f);
+                            s2 = __fmaf_rn(e, e, s2);
+                        }
+                        if (s2 > ub) break;
+                    }
                 }
                 lb = fmaxf(lb, s2);
                 if (s2 > ub) {
@@ -316,6 +346,10 @@ search_kernel(const SearchArgs A) {
     C.use_ec = A.use_lb;
     C.ur = A.ur;
     C.lr = A.lr;
+    C.eu = nullptr;
+    C.el = nullptr;
+    C.ec_w = 0;
+    C.ec_d = 0;
     C.lb_scale = A.lb_scale;
     C.bsf = A.bsf;
     C.nw = A.nw;
