@@ -17,15 +17,19 @@
 #include <cstdint>
 
 #include "common.cuh"
+#include "eapdtw.h"
 #include "search_kernel.cuh"
 
 namespace eapdtw {
 
 constexpr int kBatchLevels = 5;      // K = 4, 8, 16, 32, then the four-window level
 constexpr int kBatchClasses = 12;    // first levels 0..3 x band modes 0..2
+constexpr int kSeedClasses = 6;      // seed passes: K = 32 (m <= 1024) or four windows, x band modes
+constexpr int kAllClasses = kBatchClasses + kSeedClasses;
 constexpr int kBatchSeedBest = 32;   // sampled windows per item run through exact DTW
 constexpr int kBatchSeedSamples = 4096;
 constexpr int kBatchSlots = 64;      // k-best slots per item (k <= 64)
+constexpr size_t kWideSmem = sizeof(float) * kWarpsPerBlock * EAPDTW_MAX_QUERY;  // query copies, WIDE
 
 __host__ __device__ constexpr int batch_level_K(int level) { return level < 4 ? (4 << level) : 32; }
 
@@ -66,8 +70,8 @@ struct BatchDev {
     const int* nslots;           // [1]
     const int* kstride;          // [1] result row length
     const BatchItem* items;      // [cap_items]
-    const BatchClass* classes;   // [kBatchClasses]
-    const int* citems;           // [cap_items]
+    const BatchClass* classes;   // [kAllClasses]
+    const int* citems;           // [2 * cap_items]: tile classes, then seed classes
     const int64_t* cprefix;      // [cap_items + kBatchClasses]
     const int64_t* sprefix;      // [cap_items + 1] seed sample prefix
     const QuerySlot* qslots;     // [cap_slots]
@@ -90,6 +94,7 @@ struct BatchLaunch {
     int level;
     int band;
     int cls;                    // class of items whose first level this is (-1: none)
+    int scls;                   // seed class whose seed windows this launch runs (-1: none)
     const long long* rr_in;     // re-run entries (item << 32 | window) for this level and band
     const int* rr_in_count;
     long long* rr_out;          // next level's lists: rr_out + b * rr_cap for band b
@@ -101,15 +106,24 @@ struct BatchLaunch {
 };
 
 // Persistent batch kernel: the cascade and wavefront of process_tile, the
-// query and the windows read from global memory (items differ in length).
+// windows read from global memory (items differ in length).  The query is
+// read from global memory too, except at the four-window level (WIDE), which
+// streams the column values at every step: there each warp first copies the
+// item's query into its slot of dynamic shared memory (kMaxQuery floats).
+// A seed launch (scls >= 0) runs the seed windows of its class, before any
+// tile: their exact distances tighten each item's bound, as the one-query
+// search's seed pass does.  It runs at the widest level, where no live region
+// overflows.
 template <int K, int BAND, bool WIDE>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32, WIDE ? 1 : search_min_blocks(K, BAND))
 batch_kernel(const BatchLaunch L) {
     __shared__ unsigned long long s_cnt[kNumCounters];
+    extern __shared__ __align__(16) float s_q[];
     if (threadIdx.x < kNumCounters) s_cnt[threadIdx.x] = 0;
     __syncthreads();
     const int lane = threadIdx.x & 31;
-    int cn = 0, c0 = 0;
+    const int warp = threadIdx.x >> 5;
+    int cn = 0, c0 = 0, sn = 0, s0 = 0;
     int64_t ntiles = 0;
     const int64_t* P = nullptr;
     if (L.cls >= 0) {
@@ -119,7 +133,12 @@ batch_kernel(const BatchLaunch L) {
         P = L.D.cprefix + c.item_off + L.cls;
         ntiles = P[cn];
     }
-    const int64_t nseed = static_cast<int64_t>(cn) * kBatchSeedBest;
+    if (L.scls >= 0) {
+        const BatchClass c = L.D.classes[L.scls];
+        sn = c.nitems;
+        s0 = c.item_off;
+    }
+    const int64_t nseed = static_cast<int64_t>(sn) * kBatchSeedBest;
     int nrr = 0;
     if (L.rr_in) {
         const int c = *L.rr_in_count;
@@ -138,7 +157,7 @@ batch_kernel(const BatchLaunch L) {
         if (su < nseed) {
             const int j = static_cast<int>(su / kBatchSeedBest);
             const int s = static_cast<int>(su % kBatchSeedBest);
-            item = L.D.citems[c0 + j];
+            item = L.D.citems[s0 + j];
             if (s >= L.D.nbest[item]) continue;
             i0 = L.D.best[static_cast<int64_t>(item) * kBatchSeedBest + s] & 0xffffffffll;
             list = true;
@@ -165,6 +184,13 @@ batch_kernel(const BatchLaunch L) {
         TileCtx C;
         C.ref = it.ref;
         C.zq = it.zq;
+        if (WIDE) {
+            float* q = s_q + warp * EAPDTW_MAX_QUERY;
+            __syncwarp();
+            for (int j = lane; j < it.m; j += 32) q[j] = it.zq[j];
+            __syncwarp();
+            C.zq = q;
+        }
         C.uq = it.uq;
         C.lq = it.lq;
         C.zqo = it.zqo;
@@ -182,12 +208,13 @@ batch_kernel(const BatchLaunch L) {
         C.lb_scale = L.lb_scale;
         C.bsf = BestSoFar{L.D.slots + static_cast<int64_t>(item) * kBatchSlots, L.D.ub_seed + item, it.k, 0, 0.0f};
         C.nw = it.nw;
-        const int bn = it.band_next[L.level];
+        const bool seed = su < nseed;
+        const int bn = seed ? -1 : it.band_next[L.level];
         C.ovf_out = bn >= 0 ? L.rr_out + static_cast<int64_t>(bn) * L.rr_cap : nullptr;
         C.ovf_out_count = bn >= 0 ? L.rr_out_count + bn : nullptr;
         C.ovf_cap = bn >= 0 ? L.rr_cap : 0;
         C.tag = static_cast<long long>(item) << 32;
-        C.lost = L.D.flags + item;
+        C.lost = seed ? nullptr : L.D.flags + item;   // a seed is only a hint: nothing is lost
         C.dbg = nullptr;
         process_tile<K, BAND, !WIDE, WIDE, false, 2>(C, nullptr, list, i0, nl, count);
     }

@@ -7,13 +7,14 @@ namespace eapdtw {
 namespace {
 template <int BAND>
 cudaError_t launch_band(const BatchLaunch& args, int blocks, cudaStream_t s) {
-    batch_kernel<32, BAND, true><<<blocks, kWarpsPerBlock * 32, 0, s>>>(args);
+    batch_kernel<32, BAND, true><<<blocks, kWarpsPerBlock * 32, kWideSmem, s>>>(args);
     return cudaGetLastError();
 }
 template <int BAND>
 int occupancy_blocks() {
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel<32, BAND, true>, kWarpsPerBlock * 32, 0) !=
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel<32, BAND, true>, kWarpsPerBlock * 32,
+                                                      kWideSmem) !=
         cudaSuccess)
         per_sm = 1;
     int dev = 0, sms = 0;
@@ -23,8 +24,9 @@ int occupancy_blocks() {
 }
 template <int BAND>
 cudaError_t attributes() {
-    // the windows and the query are read through L1: give it the whole carveout
-    return cudaFuncSetAttribute(batch_kernel<32, BAND, true>, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
+    // the query copies of the eight warps live in dynamic shared memory
+    return cudaFuncSetAttribute(batch_kernel<32, BAND, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                static_cast<int>(kWideSmem));
 }
 }  // namespace
 

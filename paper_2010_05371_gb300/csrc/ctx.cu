@@ -25,7 +25,7 @@ namespace {
 
 constexpr float kLbScale = 1.0001f;   // prune iff lb > ub * kLbScale (as subseq_search)
 constexpr int kMaxQ = EAPDTW_MAX_QUERY;
-constexpr int kNumWork = kBatchLevels * 3;
+constexpr int kNumWork = kBatchLevels * 3 + kSeedClasses;
 
 int64_t al256(int64_t x) { return (x + 255) / 256 * 256; }
 
@@ -73,9 +73,9 @@ struct Layout {
     void make(int cap_items, int cap_slots) {
         hdr = 0;
         classes = 256;
-        items = al256(classes + sizeof(BatchClass) * kBatchClasses);
+        items = al256(classes + sizeof(BatchClass) * kAllClasses);
         citems = al256(items + sizeof(BatchItem) * static_cast<int64_t>(cap_items));
-        cprefix = al256(citems + sizeof(int) * static_cast<int64_t>(cap_items));
+        cprefix = al256(citems + sizeof(int) * 2 * static_cast<int64_t>(cap_items));
         sprefix = al256(cprefix + sizeof(int64_t) * static_cast<int64_t>(cap_items + kBatchClasses));
         qslots = al256(sprefix + sizeof(int64_t) * static_cast<int64_t>(cap_items + 1));
         total = al256(qslots + sizeof(QuerySlot) * static_cast<int64_t>(cap_slots));
@@ -113,7 +113,7 @@ struct eapdtw_ctx {
     int64_t* res_idx = nullptr;
     double* res_dist = nullptr;
     long long* rr = nullptr;             // [2][3][rr_cap]
-    unsigned char* small = nullptr;      // rr counts [8] | work [16] | counters [16]
+    unsigned char* small = nullptr;      // rr counts [8] | work [32] | counters [16]
     int* h_flags = nullptr;              // pinned: item flags, then query flags, then counters
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -127,7 +127,8 @@ struct eapdtw_ctx {
 
     int* rr_counts() { return reinterpret_cast<int*>(small); }
     unsigned long long* work() { return reinterpret_cast<unsigned long long*>(small + 64); }
-    unsigned long long* counters() { return reinterpret_cast<unsigned long long*>(small + 192); }
+    unsigned long long* counters() { return reinterpret_cast<unsigned long long*>(small + 320); }
+    unsigned long long* seed_counters() { return reinterpret_cast<unsigned long long*>(small + 448); }
 };
 
 namespace {
@@ -220,7 +221,7 @@ int32_t ensure_arena(eapdtw_ctx* c, int n, int nslots, int64_t qf, int64_t sampl
                     dalloc(c->nbest, ci, bytes) && dalloc(c->best, ci * kBatchSeedBest, bytes) &&
                     dalloc(c->flags, ci, bytes) && dalloc(c->seed_ed, cm, bytes) && dalloc(c->seed_idx, cm, bytes) &&
                     dalloc(c->res_idx, rows, bytes) && dalloc(c->res_dist, rows, bytes) &&
-                    dalloc(c->rr, 6 * cr, bytes) && dalloc(c->small, 512, bytes);
+                    dalloc(c->rr, 6 * cr, bytes) && dalloc(c->small, 1024, bytes);
     if (!ok || (c->budget > 0 && c->used + bytes > c->budget)) {
         c->arena_bytes = bytes;
         c->used += bytes;
@@ -290,9 +291,28 @@ cudaError_t batch_attrs_once() {
 cudaError_t enqueue_batch(eapdtw_ctx* c, cudaStream_t s) {
     const BatchDev D = dev_view(c);
     int* rrc = c->rr_counts();
-    cudaError_t e = launch_batch_prep(D, c->cap_items, c->counters(), kNumCounters, c->work(), kNumWork, rrc, 8,
+    cudaError_t e = launch_batch_prep(D, c->cap_items, c->counters(), 2 * kNumCounters, c->work(), kNumWork, rrc, 8,
                                       kMaxQ, s);
     if (e != cudaSuccess) return e;
+    // seed passes: K = 32 for queries up to 1024 columns, the four-window level beyond
+    for (int sc = 0; sc < kSeedClasses; ++sc) {
+        BatchLaunch L{};
+        L.D = D;
+        L.level = sc < 3 ? 3 : 4;
+        L.band = sc % 3;
+        L.cls = -1;
+        L.scls = kBatchClasses + sc;
+        L.rr_in = nullptr;
+        L.rr_in_count = rrc;
+        L.rr_out = c->rr;
+        L.rr_out_count = rrc;
+        L.rr_cap = 0;
+        L.work = c->work() + kBatchLevels * 3 + sc;
+        L.counters = c->seed_counters();
+        L.lb_scale = kLbScale;
+        e = launch_batch(L.level, L.band, L, batch_blocks(L.level, L.band), s);
+        if (e != cudaSuccess) return e;
+    }
     for (int level = 0; level < kBatchLevels; ++level) {
         const int pin = level & 1, pout = (level + 1) & 1;
         e = cudaMemsetAsync(rrc + 3 * pout, 0, sizeof(int) * 3, s);
@@ -303,6 +323,7 @@ cudaError_t enqueue_batch(eapdtw_ctx* c, cudaStream_t s) {
             L.level = level;
             L.band = band;
             L.cls = level < 4 ? level * 3 + band : -1;
+            L.scls = -1;
             L.rr_in = level > 0 ? c->rr + static_cast<int64_t>(3 * pin + band) * c->rr_cap : nullptr;
             L.rr_in_count = rrc + 3 * pin + band;
             L.rr_out = c->rr + static_cast<int64_t>(3 * pout) * c->rr_cap;
@@ -552,7 +573,7 @@ int32_t run_batch(eapdtw_ctx* c, const eapdtw_item* items, int32_t n, int32_t ks
 
     // ---- host planning: items, query slots, classes, seed samples ----------
     struct Plan1 {
-        int m, w, level0, slot, cls;
+        int m, w, level0, slot, cls, scls;
         bool unc;
         int64_t n, nw, tiles, ns;
     };
@@ -579,6 +600,7 @@ int32_t run_batch(eapdtw_ctx* c, const eapdtw_item* items, int32_t n, int32_t ks
         p.ns = p.nw >= 2048 ? std::min<int64_t>(p.nw, kBatchSeedSamples) : 0;
         p.level0 = first_level(c, p.m, p.w, p.unc);
         p.cls = p.level0 * 3 + band_mode(p.level0, p.w, p.unc);
+        p.scls = kBatchClasses + (p.m > 32 * 32 ? 3 : 0) + band_mode(3, p.w, p.unc);
         const auto key = std::make_tuple(it.Q, p.m, p.w);
         auto f = slot_of.find(key);
         if (f == slot_of.end()) {
@@ -622,10 +644,13 @@ int32_t run_batch(eapdtw_ctx* c, const eapdtw_item* items, int32_t n, int32_t ks
     int64_t* sprefix = reinterpret_cast<int64_t*>(H + L.sprefix);
     QuerySlot* hq = reinterpret_cast<QuerySlot*>(H + L.qslots);
     std::memcpy(hq, slots.data(), sizeof(QuerySlot) * nslots);
-    int cnt[kBatchClasses] = {0};
-    for (int i = 0; i < n; ++i) ++cnt[P[i].cls];
+    int cnt[kAllClasses] = {0};
+    for (int i = 0; i < n; ++i) {
+        ++cnt[P[i].cls];
+        if (P[i].ns > 0) ++cnt[P[i].scls];
+    }
     int off = 0;
-    for (int k = 0; k < kBatchClasses; ++k) {
+    for (int k = 0; k < kAllClasses; ++k) {
         cls[k].item_off = off;
         cls[k].nitems = 0;
         off += cnt[k];
@@ -669,6 +694,10 @@ int32_t run_batch(eapdtw_ctx* c, const eapdtw_item* items, int32_t n, int32_t ks
         BatchClass& k = cls[p.cls];
         const int j = k.nitems++;
         citems[k.item_off + j] = i;
+        if (p.ns > 0) {
+            BatchClass& sk = cls[p.scls];
+            citems[sk.item_off + sk.nitems++] = i;
+        }
     }
     for (int k = 0; k < kBatchClasses; ++k) {
         int64_t* pre = cprefix + cls[k].item_off + k;
@@ -679,9 +708,9 @@ int32_t run_batch(eapdtw_ctx* c, const eapdtw_item* items, int32_t n, int32_t ks
         return cudaMemcpyAsync(c->tables + o, H + o, static_cast<size_t>(bytes), cudaMemcpyHostToDevice, st);
     };
     CKC(up(L.hdr, 64));
-    CKC(up(L.classes, sizeof(BatchClass) * kBatchClasses));
+    CKC(up(L.classes, sizeof(BatchClass) * kAllClasses));
     CKC(up(L.items, sizeof(BatchItem) * static_cast<int64_t>(n)));
-    CKC(up(L.citems, sizeof(int) * static_cast<int64_t>(n)));
+    CKC(up(L.citems, sizeof(int) * static_cast<int64_t>(off)));
     CKC(up(L.cprefix, sizeof(int64_t) * static_cast<int64_t>(n + kBatchClasses)));
     CKC(up(L.sprefix, sizeof(int64_t) * static_cast<int64_t>(n + 1)));
     CKC(up(L.qslots, sizeof(QuerySlot) * static_cast<int64_t>(nslots)));
