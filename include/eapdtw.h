@@ -47,6 +47,9 @@ extern "C" {
 #define EAPDTW_ERR_TIMEOUT -5       /* a device-side wait exceeded its budget */
 #define EAPDTW_ERR_UNSUPPORTED -6   /* size beyond what this build supports (see each call) */
 #define EAPDTW_ERR_INTERNAL -7      /* a device-side consistency check failed */
+#define EAPDTW_ERR_BUSY -8          /* the object is in use (a reference read by the serving loop; a second server) */
+#define EAPDTW_ERR_CANCELLED -9     /* the serving request was cancelled */
+#define EAPDTW_PENDING 1            /* eapdtw_serve_poll: the request has not finished yet */
 
 /* Upper limits of this build.  The query (shorter series) length is bounded
  * by the query staging buffer in shared memory. */
@@ -271,6 +274,61 @@ int32_t eapdtw_get_first_tile(eapdtw_ctx* ctx, int32_t log2_m, int32_t ratio_ten
  * of signatures entered.  Blocking; results of later searches are unchanged. */
 int32_t eapdtw_autotune(eapdtw_ctx* ctx, const eapdtw_item* items, int32_t n, int64_t sample_windows,
                         void* stream, int32_t* n_tuned);
+
+/* ------------------------------------------------------------------------
+ * Serving loop (continuous batching).
+ *
+ * Not in the paper: a server thread of the context takes requests from any
+ * host thread and runs them in rounds of the batched launch sequence.  Each
+ * round processes the next chunk_windows windows of every admitted request,
+ * so a request that arrives while others are on the GPU is admitted at the
+ * next round boundary (a free state slot and the memory it needs, see below)
+ * and its work overlaps with theirs.  The references, their window
+ * statistics and each admitted request's state (prepared query, seed bound,
+ * k-best list) stay on the device across rounds.  A request's result is
+ * exactly subseq_search of its (Q, R, w, k), whatever else runs with it.
+ * Admission: up to max_active requests hold a state slot; a request whose
+ * LB_Keogh EC needs a running-extrema level of its reference that does not
+ * fit the context's memory budget finishes with EAPDTW_ERR_OUT_OF_MEMORY.
+ * ------------------------------------------------------------------------ */
+
+/* eapdtw_serve_start - start the server thread (one per context): max_active
+ * state slots (1..4096), chunk_windows windows per request per round (>= 32,
+ * rounded up to a multiple of 32).  Reserves its arena (tables, re-run lists
+ * for max_active * chunk_windows windows, result rows) within the budget. */
+int32_t eapdtw_serve_start(eapdtw_ctx* ctx, int32_t max_active, int64_t chunk_windows);
+
+/* eapdtw_serve_stop - stop the server thread after its current round and free
+ * its arena; requests not yet polled are dropped.  No thread may be inside
+ * eapdtw_serve_poll while it runs. */
+int32_t eapdtw_serve_stop(eapdtw_ctx* ctx);
+
+/* eapdtw_serve_submit - queue a request: Q is a HOST array of lQ values
+ * (copied before the call returns), searched in reference ref_id with window
+ * w for the k best windows (k <= EAPDTW_MAX_K), lower bounds skipped if
+ * no_lb.  *req_id receives its handle.  Never blocks on the GPU. */
+int32_t eapdtw_serve_submit(eapdtw_ctx* ctx, const float* Q, int64_t lQ, int32_t ref_id, int64_t w, int32_t k,
+                            int32_t no_lb, int64_t* req_id);
+
+/* eapdtw_serve_poll - the state of a request, waiting up to timeout_ms
+ * milliseconds (0: do not wait) for it to finish.  EAPDTW_PENDING: not done.
+ * EAPDTW_OK: out_idx/out_dist (HOST, k entries; either may be NULL) and
+ * *latency_ns (submission to completion; may be NULL) are filled and the
+ * handle is released.  A negative code (the request failed, or
+ * EAPDTW_ERR_CANCELLED) also releases the handle. */
+int32_t eapdtw_serve_poll(eapdtw_ctx* ctx, int64_t req_id, int64_t* out_idx, double* out_dist, int64_t* latency_ns,
+                          int32_t timeout_ms);
+
+/* eapdtw_serve_cancel - cancel a request: a queued one at once, an admitted
+ * one at the next round boundary.  Poll it to release the handle. */
+int32_t eapdtw_serve_cancel(eapdtw_ctx* ctx, int64_t req_id);
+
+/* eapdtw_serve_stats - out[0..min(nout, EAPDTW_SERVE_NSTATS)): completed,
+ * cancelled, queued, admitted, rounds, windows processed, p50 and p99 latency
+ * of the completed requests (ns, -1 if none), requests re-run alone, sticky
+ * CUDA error of the loop (0 if none). */
+#define EAPDTW_SERVE_NSTATS 10
+int32_t eapdtw_serve_stats(eapdtw_ctx* ctx, int64_t* out, int32_t nout);
 
 #ifdef __cplusplus
 }

@@ -52,6 +52,10 @@ class Item(C.Structure):
     ]
 
 
+PENDING = 1
+SERVE_STAT_NAMES = ("completed", "cancelled", "queued", "admitted", "rounds", "windows", "p50_ns", "p99_ns",
+                    "reruns", "error")
+
 CTX_INFO_NAMES = ("bytes_held", "budget", "live_refs", "arena_bytes", "batches", "items_run",
                   "items_rerun", "graph_captured")
 
@@ -114,6 +118,19 @@ def lib():
         L.eapdtw_get_first_tile.argtypes = [vp, i32, i32, i32, pi32]
         L.eapdtw_autotune.restype = i32
         L.eapdtw_autotune.argtypes = [vp, C.POINTER(Item), i32, i64, vp, pi32]
+        pi64 = C.POINTER(i64)
+        L.eapdtw_serve_start.restype = i32
+        L.eapdtw_serve_start.argtypes = [vp, i32, i64]
+        L.eapdtw_serve_stop.restype = i32
+        L.eapdtw_serve_stop.argtypes = [vp]
+        L.eapdtw_serve_submit.restype = i32
+        L.eapdtw_serve_submit.argtypes = [vp, vp, i64, i32, i64, i32, i32, pi64]
+        L.eapdtw_serve_poll.restype = i32
+        L.eapdtw_serve_poll.argtypes = [vp, i64, vp, vp, pi64, i32]
+        L.eapdtw_serve_cancel.restype = i32
+        L.eapdtw_serve_cancel.argtypes = [vp, i64]
+        L.eapdtw_serve_stats.restype = i32
+        L.eapdtw_serve_stats.argtypes = [vp, pi64, i32]
         _lib = L
     return _lib
 
@@ -368,3 +385,40 @@ class Context:
         _check(lib().eapdtw_get_first_tile(self._h, int(log2_m), int(ratio_tenths), int(band), C.byref(t)),
                "eapdtw_get_first_tile")
         return t.value
+
+    # ---- serving loop -----------------------------------------------------
+    def serve_start(self, max_active: int = 64, chunk_windows: int = 1 << 22):
+        """Start the context's server thread (continuous batching in rounds)."""
+        _check(lib().eapdtw_serve_start(self._h, int(max_active), int(chunk_windows)), "eapdtw_serve_start")
+
+    def serve_stop(self):
+        _check(lib().eapdtw_serve_stop(self._h), "eapdtw_serve_stop")
+
+    def submit(self, Q, ref_id: int, w: int, k: int = 1, no_lb: bool = False) -> int:
+        """Queue a request (Q: host array, copied); returns its id."""
+        q = np.ascontiguousarray(Q, dtype=np.float32)
+        rid = C.c_int64(0)
+        _check(lib().eapdtw_serve_submit(self._h, q.ctypes.data, len(q), int(ref_id), int(w), int(k),
+                                         int(bool(no_lb)), C.byref(rid)), "eapdtw_serve_submit")
+        return rid.value
+
+    def poll(self, req_id: int, k: int, timeout_ms: int = 0):
+        """None while the request runs; else (idx[k], dist[k], latency_ns), releasing it.
+        Raises EapDtwError if the request failed or was cancelled."""
+        idx = np.empty(k, dtype=np.int64)
+        dist = np.empty(k, dtype=np.float64)
+        lat = C.c_int64(0)
+        rc = lib().eapdtw_serve_poll(self._h, int(req_id), idx.ctypes.data, dist.ctypes.data, C.byref(lat),
+                                     int(timeout_ms))
+        if rc == PENDING:
+            return None
+        _check(rc, "eapdtw_serve_poll")
+        return idx, dist, lat.value
+
+    def cancel(self, req_id: int):
+        _check(lib().eapdtw_serve_cancel(self._h, int(req_id)), "eapdtw_serve_cancel")
+
+    def serve_stats(self) -> dict:
+        out = (C.c_int64 * len(SERVE_STAT_NAMES))()
+        _check(lib().eapdtw_serve_stats(self._h, out, len(SERVE_STAT_NAMES)), "eapdtw_serve_stats")
+        return dict(zip(SERVE_STAT_NAMES, (int(v) for v in out)))

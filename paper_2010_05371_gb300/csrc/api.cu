@@ -368,6 +368,9 @@ const char* eapdtw_strerror(int32_t code) {
         case EAPDTW_ERR_TIMEOUT: return "device wait timed out";
         case EAPDTW_ERR_UNSUPPORTED: return "size not supported by this build";
         case EAPDTW_ERR_INTERNAL: return "internal consistency check failed";
+        case EAPDTW_ERR_BUSY: return "in use";
+        case EAPDTW_ERR_CANCELLED: return "request cancelled";
+        case EAPDTW_PENDING: return "pending";
         default: return "unknown error code";
     }
 }

@@ -41,7 +41,11 @@ struct BatchItem {
     const float* zqo;
     const int* ord;
     int64_t nw;          // windows n - m + 1
+    int64_t win0;        // this launch sequence covers windows [win0, win0 + nwin)
+    int64_t nwin;
     int64_t seed_off;    // first sample of this item in the seed sample arrays
+    int state;           // slot of the item's resident state (k-best list, seed bound, flags)
+    int fresh;           // 1: the state starts from empty in this launch sequence
     int m, w, k, use_lb;
     int seed_ns;         // sampled windows (0: no seed)
     int level0;          // first level
@@ -77,11 +81,12 @@ struct BatchDev {
     const QuerySlot* qslots;     // [cap_slots]
     float* qarena;               // 5 arrays of mp floats per slot (ord stored as int)
     int* qbad;                   // [cap_slots] non-finite query values
-    unsigned long long* slots;   // [cap_items * kBatchSlots]
-    float* ub_seed;              // [cap_items]
-    int* nbest;                  // [cap_items]
-    long long* best;             // [cap_items * kBatchSeedBest]
-    int* flags;                  // [cap_items] bit 0: an overflow entry was lost
+    // resident per-state arrays (indexed by BatchItem::state)
+    unsigned long long* slots;   // [cap_states * kBatchSlots]
+    float* ub_seed;              // [cap_states]
+    int* nbest;                  // [cap_states]
+    long long* best;             // [cap_states * kBatchSeedBest]
+    int* flags;                  // [cap_states] bit 0: an overflow entry was lost
     float* seed_ed;              // [cap_samples]
     int* seed_idx;               // [cap_samples]
     int64_t* res_idx;            // [cap_items * kstride]
@@ -158,8 +163,9 @@ batch_kernel(const BatchLaunch L) {
             const int j = static_cast<int>(su / kBatchSeedBest);
             const int s = static_cast<int>(su % kBatchSeedBest);
             item = L.D.citems[s0 + j];
-            if (s >= L.D.nbest[item]) continue;
-            i0 = L.D.best[static_cast<int64_t>(item) * kBatchSeedBest + s] & 0xffffffffll;
+            const int st = L.D.items[item].state;
+            if (s >= L.D.nbest[st]) continue;
+            i0 = L.D.best[static_cast<int64_t>(st) * kBatchSeedBest + s] & 0xffffffffll;
             list = true;
         } else if (su < nseed + nrr) {
             const long long e = L.rr_in[su - nseed];
@@ -176,11 +182,14 @@ batch_kernel(const BatchLaunch L) {
                 else hi = mid;
             }
             item = L.D.citems[c0 + lo];
-            i0 = (t - P[lo]) * 32;
+            i0 = L.D.items[item].win0 + (t - P[lo]) * 32;
             list = false;
         }
         const BatchItem& it = L.D.items[item];
-        if (!list) nl = static_cast<int>(it.nw - i0 < 32 ? it.nw - i0 : 32);
+        if (!list) {
+            const int64_t end = it.win0 + it.nwin;
+            nl = static_cast<int>(end - i0 < 32 ? end - i0 : 32);
+        }
         TileCtx C;
         C.ref = it.ref;
         C.zq = it.zq;
@@ -206,7 +215,8 @@ batch_kernel(const BatchLaunch L) {
         C.ec_w = it.ec_w;
         C.ec_d = it.ec_d;
         C.lb_scale = L.lb_scale;
-        C.bsf = BestSoFar{L.D.slots + static_cast<int64_t>(item) * kBatchSlots, L.D.ub_seed + item, it.k, 0, 0.0f};
+        C.bsf = BestSoFar{L.D.slots + static_cast<int64_t>(it.state) * kBatchSlots, L.D.ub_seed + it.state, it.k, 0,
+                          0.0f};
         C.nw = it.nw;
         const bool seed = su < nseed;
         const int bn = seed ? -1 : it.band_next[L.level];
@@ -214,7 +224,7 @@ batch_kernel(const BatchLaunch L) {
         C.ovf_out_count = bn >= 0 ? L.rr_out_count + bn : nullptr;
         C.ovf_cap = bn >= 0 ? L.rr_cap : 0;
         C.tag = static_cast<long long>(item) << 32;
-        C.lost = seed ? nullptr : L.D.flags + item;   // a seed is only a hint: nothing is lost
+        C.lost = seed ? nullptr : L.D.flags + it.state;   // a seed is only a hint: nothing is lost
         C.dbg = nullptr;
         process_tile<K, BAND, !WIDE, WIDE, false, 2>(C, nullptr, list, i0, nl, count);
     }

@@ -16,122 +16,17 @@
 #include <cuda_runtime.h>
 
 #include "batch.cuh"
+#include "ctx_internal.h"
 #include "eapdtw.h"
 #include "kernels.h"
 
-using namespace eapdtw;
+namespace eapdtw {
+
+int32_t server_shutdown(eapdtw_ctx* c);  // serve.cu
 
 namespace {
-
-constexpr float kLbScale = 1.0001f;   // prune iff lb > ub * kLbScale (as subseq_search)
-constexpr int kMaxQ = EAPDTW_MAX_QUERY;
-constexpr int kNumWork = kBatchLevels * 3 + kSeedClasses;
 
 int64_t al256(int64_t x) { return (x + 255) / 256 * 256; }
-
-constexpr int kEnvLevels = 13;   // running extrema over 2^p points, p = 0..12 (radius <= 4095)
-
-struct RefEntry {
-    bool live = false;
-    float* R = nullptr;
-    int64_t n = 0;
-    double *P1 = nullptr, *P2 = nullptr, *T1 = nullptr, *T2 = nullptr;
-    float* A = nullptr;
-    int64_t bytes = 0;
-    // sparse table of running maxima / minima for LB_Keogh EC, built on demand;
-    // level 0 is R itself
-    float* emax[kEnvLevels] = {nullptr};
-    float* emin[kEnvLevels] = {nullptr};
-    int env_levels = 1;
-};
-
-void free_ref(RefEntry& r) {
-    for (int p = 1; p < kEnvLevels; ++p) {
-        if (r.emax[p]) cudaFree(r.emax[p]);
-        if (r.emin[p]) cudaFree(r.emin[p]);
-    }
-    if (r.R) cudaFree(r.R);
-    if (r.P1) cudaFree(r.P1);
-    if (r.P2) cudaFree(r.P2);
-    if (r.T1) cudaFree(r.T1);
-    if (r.T2) cudaFree(r.T2);
-    if (r.A) cudaFree(r.A);
-    r = RefEntry{};
-}
-
-// Level of the table for envelope radius r: the largest p with 2^p <= 2r + 1.
-int env_level(int r) {
-    int p = 0;
-    while ((2 << p) <= 2 * r + 1) ++p;
-    return p;
-}
-
-// Byte offsets of the work tables (the same layout on the host staging buffer
-// and on the device).
-struct Layout {
-    int64_t hdr = 0, classes = 0, items = 0, citems = 0, cprefix = 0, sprefix = 0, qslots = 0, total = 0;
-    void make(int cap_items, int cap_slots) {
-        hdr = 0;
-        classes = 256;
-        items = al256(classes + sizeof(BatchClass) * kAllClasses);
-        citems = al256(items + sizeof(BatchItem) * static_cast<int64_t>(cap_items));
-        cprefix = al256(citems + sizeof(int) * 2 * static_cast<int64_t>(cap_items));
-        sprefix = al256(cprefix + sizeof(int64_t) * static_cast<int64_t>(cap_items + kBatchClasses));
-        qslots = al256(sprefix + sizeof(int64_t) * static_cast<int64_t>(cap_items + 1));
-        total = al256(qslots + sizeof(QuerySlot) * static_cast<int64_t>(cap_slots));
-    }
-};
-
-}  // namespace
-
-struct eapdtw_ctx {
-    int device = 0;
-    int64_t budget = 0;        // bytes (0: no limit of the context's own)
-    int64_t used = 0;          // bytes held: references and the batch arena
-    std::mutex mu;
-    std::vector<RefEntry> refs;
-    cudaStream_t cap_stream = nullptr;   // stream the launch sequence is captured on
-
-    // batch arena (capacities; grown on demand, never shrunk)
-    int cap_items = 0, cap_slots = 0;
-    int64_t cap_qf = 0, cap_samples = 0;
-    int rr_cap = 0;
-    int64_t rr_cap_max = 1 << 25;        // entries per re-run list (a fuller list marks items for a re-run)
-    int64_t arena_bytes = 0;
-    Layout lay;
-    unsigned char* tables = nullptr;     // device
-    unsigned char* htables = nullptr;    // pinned host staging
-    float* qarena = nullptr;
-    int* qbad = nullptr;
-    unsigned long long* slots = nullptr;
-    float* ub_seed = nullptr;
-    int* nbest = nullptr;
-    long long* best = nullptr;
-    int* flags = nullptr;
-    float* seed_ed = nullptr;
-    int* seed_idx = nullptr;
-    int64_t* res_idx = nullptr;
-    double* res_dist = nullptr;
-    long long* rr = nullptr;             // [2][3][rr_cap]
-    unsigned char* small = nullptr;      // rr counts [8] | work [32] | counters [16]
-    int* h_flags = nullptr;              // pinned: item flags, then query flags, then counters
-    cudaGraph_t graph = nullptr;
-    cudaGraphExec_t exec = nullptr;
-    cudaEvent_t ev0 = nullptr, ev1 = nullptr;   // around the graph launch (autotuner timing)
-
-    // K of the first level per (log2 m, window ratio in tenths, band mode), set by the autotuner
-    std::map<std::tuple<int, int, int>, int> tuned;
-
-    // statistics
-    int64_t batches = 0, items_run = 0, items_rerun = 0;
-
-    int* rr_counts() { return reinterpret_cast<int*>(small); }
-    unsigned long long* work() { return reinterpret_cast<unsigned long long*>(small + 64); }
-    unsigned long long* counters() { return reinterpret_cast<unsigned long long*>(small + 320); }
-    unsigned long long* seed_counters() { return reinterpret_cast<unsigned long long*>(small + 448); }
-};
-
-namespace {
 
 #define CKC(expr)                    \
     do {                             \
@@ -140,20 +35,6 @@ namespace {
             return EAPDTW_ERR_CUDA;  \
         }                            \
     } while (0)
-
-// Runs the body with the context's device current, then restores the caller's.
-struct DeviceGuard {
-    int prev = -1;
-    bool ok = false;
-    explicit DeviceGuard(int dev) {
-        if (cudaGetDevice(&prev) != cudaSuccess) { cudaGetLastError(); return; }
-        ok = prev == dev || cudaSetDevice(dev) == cudaSuccess;
-        if (!ok) cudaGetLastError();
-    }
-    ~DeviceGuard() {
-        if (prev >= 0) cudaSetDevice(prev);
-    }
-};
 
 template <typename T>
 void dfree(T*& p) {
@@ -174,27 +55,13 @@ bool dalloc(T*& p, int64_t count, int64_t& bytes) {
     return true;
 }
 
-void drop_graph(eapdtw_ctx* c) {
-    if (c->exec) cudaGraphExecDestroy(c->exec);
-    if (c->graph) cudaGraphDestroy(c->graph);
-    c->exec = nullptr;
-    c->graph = nullptr;
-}
-
-void free_arena(eapdtw_ctx* c) {
-    drop_graph(c);
-    dfree(c->tables); dfree(c->qarena); dfree(c->qbad); dfree(c->slots); dfree(c->ub_seed);
-    dfree(c->nbest); dfree(c->best); dfree(c->flags); dfree(c->seed_ed); dfree(c->seed_idx);
-    dfree(c->res_idx); dfree(c->res_dist); dfree(c->rr); dfree(c->small);
-    if (c->htables) cudaFreeHost(c->htables);
-    if (c->h_flags) cudaFreeHost(c->h_flags);
-    c->htables = nullptr;
-    c->h_flags = nullptr;
-    c->used -= c->arena_bytes;
-    c->arena_bytes = 0;
-    c->cap_items = c->cap_slots = 0;
-    c->cap_qf = c->cap_samples = 0;
-    c->rr_cap = 0;
+void free_ref(RefEntry& r) {
+    for (int p = 1; p < kEnvLevels; ++p) {
+        dfree(r.emax[p]);
+        dfree(r.emin[p]);
+    }
+    dfree(r.R); dfree(r.P1); dfree(r.P2); dfree(r.T1); dfree(r.T2); dfree(r.A);
+    r = RefEntry{};
 }
 
 int64_t grow(int64_t want, int64_t have) {
@@ -204,73 +71,36 @@ int64_t grow(int64_t want, int64_t have) {
     return c;
 }
 
-int32_t ensure_arena(eapdtw_ctx* c, int n, int nslots, int64_t qf, int64_t samples, int64_t rr_want) {
-    const int64_t ci = grow(n, c->cap_items), cs = grow(nslots, c->cap_slots);
-    const int64_t cq = grow(qf, c->cap_qf), cm = grow(samples, c->cap_samples);
-    const int64_t cr = std::max<int64_t>(std::min<int64_t>(grow(rr_want, c->rr_cap), c->rr_cap_max), 1);
-    if (ci == c->cap_items && cs == c->cap_slots && cq == c->cap_qf && cm == c->cap_samples &&
-        cr <= c->rr_cap && c->tables)
-        return EAPDTW_OK;
-    free_arena(c);
-    Layout lay;
-    lay.make(static_cast<int>(ci), static_cast<int>(cs));
-    int64_t bytes = 0;
-    const int64_t rows = ci * EAPDTW_MAX_K;
-    const bool ok = dalloc(c->tables, lay.total, bytes) && dalloc(c->qarena, cq, bytes) && dalloc(c->qbad, cs, bytes) &&
-                    dalloc(c->slots, ci * kBatchSlots, bytes) && dalloc(c->ub_seed, ci, bytes) &&
-                    dalloc(c->nbest, ci, bytes) && dalloc(c->best, ci * kBatchSeedBest, bytes) &&
-                    dalloc(c->flags, ci, bytes) && dalloc(c->seed_ed, cm, bytes) && dalloc(c->seed_idx, cm, bytes) &&
-                    dalloc(c->res_idx, rows, bytes) && dalloc(c->res_dist, rows, bytes) &&
-                    dalloc(c->rr, 6 * cr, bytes) && dalloc(c->small, 1024, bytes);
-    if (!ok || (c->budget > 0 && c->used + bytes > c->budget)) {
-        c->arena_bytes = bytes;
-        c->used += bytes;
-        free_arena(c);
-        return EAPDTW_ERR_OUT_OF_MEMORY;
-    }
-    if (cudaHostAlloc(reinterpret_cast<void**>(&c->htables), lay.total, cudaHostAllocDefault) != cudaSuccess ||
-        cudaHostAlloc(reinterpret_cast<void**>(&c->h_flags), sizeof(int) * (ci + cs) + 256, cudaHostAllocDefault) !=
-            cudaSuccess) {
-        cudaGetLastError();
-        c->arena_bytes = bytes;
-        c->used += bytes;
-        free_arena(c);
-        return EAPDTW_ERR_OUT_OF_MEMORY;
-    }
-    c->lay = lay;
-    c->cap_items = static_cast<int>(ci);
-    c->cap_slots = static_cast<int>(cs);
-    c->cap_qf = cq;
-    c->cap_samples = cm;
-    c->rr_cap = static_cast<int>(cr);
-    c->arena_bytes = bytes;
-    c->used += bytes;
-    return EAPDTW_OK;
+void drop_graph(Arena& a) {
+    if (a.exec) cudaGraphExecDestroy(a.exec);
+    if (a.graph) cudaGraphDestroy(a.graph);
+    a.exec = nullptr;
+    a.graph = nullptr;
 }
 
-BatchDev dev_view(eapdtw_ctx* c) {
+BatchDev dev_view(Arena& a) {
     BatchDev D{};
-    const Layout& L = c->lay;
-    D.nitems = reinterpret_cast<const int*>(c->tables + L.hdr);
+    const Layout& L = a.lay;
+    D.nitems = reinterpret_cast<const int*>(a.tables + L.hdr);
     D.nslots = D.nitems + 1;
     D.kstride = D.nitems + 2;
-    D.classes = reinterpret_cast<const BatchClass*>(c->tables + L.classes);
-    D.items = reinterpret_cast<const BatchItem*>(c->tables + L.items);
-    D.citems = reinterpret_cast<const int*>(c->tables + L.citems);
-    D.cprefix = reinterpret_cast<const int64_t*>(c->tables + L.cprefix);
-    D.sprefix = reinterpret_cast<const int64_t*>(c->tables + L.sprefix);
-    D.qslots = reinterpret_cast<const QuerySlot*>(c->tables + L.qslots);
-    D.qarena = c->qarena;
-    D.qbad = c->qbad;
-    D.slots = c->slots;
-    D.ub_seed = c->ub_seed;
-    D.nbest = c->nbest;
-    D.best = c->best;
-    D.flags = c->flags;
-    D.seed_ed = c->seed_ed;
-    D.seed_idx = c->seed_idx;
-    D.res_idx = c->res_idx;
-    D.res_dist = c->res_dist;
+    D.classes = reinterpret_cast<const BatchClass*>(a.tables + L.classes);
+    D.items = reinterpret_cast<const BatchItem*>(a.tables + L.items);
+    D.citems = reinterpret_cast<const int*>(a.tables + L.citems);
+    D.cprefix = reinterpret_cast<const int64_t*>(a.tables + L.cprefix);
+    D.sprefix = reinterpret_cast<const int64_t*>(a.tables + L.sprefix);
+    D.qslots = reinterpret_cast<const QuerySlot*>(a.tables + L.qslots);
+    D.qarena = a.qarena;
+    D.qbad = a.qbad;
+    D.slots = a.slots;
+    D.ub_seed = a.ub_seed;
+    D.nbest = a.nbest;
+    D.best = a.best;
+    D.flags = a.flags;
+    D.seed_ed = a.seed_ed;
+    D.seed_idx = a.seed_idx;
+    D.res_idx = a.res_idx;
+    D.res_dist = a.res_dist;
     return D;
 }
 
@@ -281,18 +111,18 @@ cudaError_t batch_attrs_once() {
     cudaGetDevice(&dev);
     if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
     std::call_once(once[dev], [&] {
-        err[dev] = batch_prep_attributes(kMaxQ);
+        err[dev] = batch_prep_attributes(EAPDTW_MAX_QUERY);
         if (err[dev] == cudaSuccess) err[dev] = batch_attributes();
     });
     return err[dev];
 }
 
 // The launch sequence of one batch; every count it needs is read on the device.
-cudaError_t enqueue_batch(eapdtw_ctx* c, cudaStream_t s) {
-    const BatchDev D = dev_view(c);
-    int* rrc = c->rr_counts();
-    cudaError_t e = launch_batch_prep(D, c->cap_items, c->counters(), 2 * kNumCounters, c->work(), kNumWork, rrc, 8,
-                                      kMaxQ, s);
+cudaError_t enqueue_sequence(Arena& a, cudaStream_t s) {
+    const BatchDev D = dev_view(a);
+    int* rrc = a.rr_counts();
+    cudaError_t e = launch_batch_prep(D, a.cap_items, a.counters(), 2 * kNumCounters, a.work(), kNumWork, rrc, 8,
+                                      EAPDTW_MAX_QUERY, s);
     if (e != cudaSuccess) return e;
     // seed passes: K = 32 for queries up to 1024 columns, the four-window level beyond
     for (int sc = 0; sc < kSeedClasses; ++sc) {
@@ -304,12 +134,12 @@ cudaError_t enqueue_batch(eapdtw_ctx* c, cudaStream_t s) {
         L.scls = kBatchClasses + sc;
         L.rr_in = nullptr;
         L.rr_in_count = rrc;
-        L.rr_out = c->rr;
+        L.rr_out = a.rr;
         L.rr_out_count = rrc;
         L.rr_cap = 0;
-        L.work = c->work() + kBatchLevels * 3 + sc;
-        L.counters = c->seed_counters();
-        L.lb_scale = kLbScale;
+        L.work = a.work() + kBatchLevels * 3 + sc;
+        L.counters = a.seed_counters();
+        L.lb_scale = kBatchLbScale;
         e = launch_batch(L.level, L.band, L, batch_blocks(L.level, L.band), s);
         if (e != cudaSuccess) return e;
     }
@@ -324,14 +154,14 @@ cudaError_t enqueue_batch(eapdtw_ctx* c, cudaStream_t s) {
             L.band = band;
             L.cls = level < 4 ? level * 3 + band : -1;
             L.scls = -1;
-            L.rr_in = level > 0 ? c->rr + static_cast<int64_t>(3 * pin + band) * c->rr_cap : nullptr;
+            L.rr_in = level > 0 ? a.rr + static_cast<int64_t>(3 * pin + band) * a.rr_cap : nullptr;
             L.rr_in_count = rrc + 3 * pin + band;
-            L.rr_out = c->rr + static_cast<int64_t>(3 * pout) * c->rr_cap;
+            L.rr_out = a.rr + static_cast<int64_t>(3 * pout) * a.rr_cap;
             L.rr_out_count = rrc + 3 * pout;
-            L.rr_cap = c->rr_cap;
-            L.work = c->work() + level * 3 + band;
-            L.counters = c->counters();
-            L.lb_scale = kLbScale;
+            L.rr_cap = a.rr_cap;
+            L.work = a.work() + level * 3 + band;
+            L.counters = a.counters();
+            L.lb_scale = kBatchLbScale;
             e = launch_batch(level, band, L, batch_blocks(level, band), s);
             if (e != cudaSuccess) return e;
         }
@@ -339,204 +169,71 @@ cudaError_t enqueue_batch(eapdtw_ctx* c, cudaStream_t s) {
     return launch_batch_finalize(D, s);
 }
 
-int32_t ensure_graph(eapdtw_ctx* c) {
-    if (c->exec) return EAPDTW_OK;
+int32_t ensure_graph(Arena& a) {
+    if (a.exec) return EAPDTW_OK;
     if (batch_attrs_once() != cudaSuccess) { cudaGetLastError(); return EAPDTW_ERR_CUDA; }
     // occupancy queries before the capture (they are not stream work)
     for (int level = 0; level < kBatchLevels; ++level)
         for (int band = 0; band < 3; ++band) batch_blocks(level, band);
-    if (cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    if (!a.cap_stream && cudaStreamCreateWithFlags(&a.cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
         cudaGetLastError();
         return EAPDTW_ERR_CUDA;
     }
-    const cudaError_t e = enqueue_batch(c, c->cap_stream);
+    if (cudaStreamBeginCapture(a.cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        cudaGetLastError();
+        return EAPDTW_ERR_CUDA;
+    }
+    const cudaError_t e = enqueue_sequence(a, a.cap_stream);
     cudaGraph_t g = nullptr;
-    const cudaError_t e2 = cudaStreamEndCapture(c->cap_stream, &g);
+    const cudaError_t e2 = cudaStreamEndCapture(a.cap_stream, &g);
     if (e != cudaSuccess || e2 != cudaSuccess || !g) {
         if (g) cudaGraphDestroy(g);
         cudaGetLastError();
         return EAPDTW_ERR_CUDA;
     }
-    if (cudaGraphInstantiate(&c->exec, g, 0) != cudaSuccess) {
+    if (cudaGraphInstantiate(&a.exec, g, 0) != cudaSuccess) {
         cudaGetLastError();
         cudaGraphDestroy(g);
-        c->exec = nullptr;
+        a.exec = nullptr;
         return EAPDTW_ERR_CUDA;
     }
-    c->graph = g;
+    a.graph = g;
     return EAPDTW_OK;
-}
-
-std::tuple<int, int, int> signature(int m, int w);
-
-// First level (block width 4 << level) of a (query length, window) pair: the
-// narrowest K whose window of 32 blocks covers the band with margin, 8 (or 4
-// for short queries) when unconstrained, unless the autotuner chose otherwise.
-int first_level(const eapdtw_ctx* c, int m, int w, bool unconstrained) {
-    int K = 32;
-    if (!unconstrained) {
-        for (int k = 4; k <= 32; k *= 2)
-            if ((2 * w + k) / (k + 1) + 3 <= 32) { K = k; break; }
-    } else {
-        K = 8;
-        for (int k = 4; k <= 8; k *= 2)
-            if (32 * k >= m) { K = k; break; }
-    }
-    auto it = c->tuned.find(signature(m, w));
-    if (it != c->tuned.end()) K = it->second;
-    int level = 0;
-    while ((4 << level) < K) ++level;
-    return level;
-}
-
-int band_mode(int level, int w, bool unconstrained) {
-    const int K = batch_level_K(level);
-    return unconstrained ? 0 : (K <= 2 * w + 2 ? 1 : 2);
 }
 
 }  // namespace
 
-extern "C" {
+void Layout::make(int cap_items, int cap_slots) {
+    hdr = 0;
+    classes = 256;
+    items = al256(classes + sizeof(BatchClass) * kAllClasses);
+    citems = al256(items + sizeof(BatchItem) * static_cast<int64_t>(cap_items));
+    cprefix = al256(citems + sizeof(int) * 2 * static_cast<int64_t>(cap_items));
+    sprefix = al256(cprefix + sizeof(int64_t) * static_cast<int64_t>(cap_items + kBatchClasses));
+    qslots = al256(sprefix + sizeof(int64_t) * static_cast<int64_t>(cap_items + 1));
+    total = al256(qslots + sizeof(QuerySlot) * static_cast<int64_t>(cap_slots));
+}
 
-int32_t eapdtw_ctx_create(int32_t device, int64_t mem_budget, eapdtw_ctx** out) {
-    if (!out || mem_budget < 0) return EAPDTW_ERR_INVALID_ARG;
-    *out = nullptr;
-    int ndev = 0;
-    if (cudaGetDeviceCount(&ndev) != cudaSuccess) { cudaGetLastError(); return EAPDTW_ERR_CUDA; }
-    if (device < 0 || device >= ndev) return EAPDTW_ERR_INVALID_ARG;
-    eapdtw_ctx* c = new (std::nothrow) eapdtw_ctx;
-    if (!c) return EAPDTW_ERR_OUT_OF_MEMORY;
-    c->device = device;
-    c->budget = mem_budget;
-    if (const char* e = std::getenv("EAPDTW_RERUN_LIST_CAP")) {
-        const long long v = std::atoll(e);
-        if (v >= 1) c->rr_cap_max = v;
-    }
-    DeviceGuard g(device);
-    if (!g.ok || cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+DeviceGuard::DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) {
         cudaGetLastError();
-        delete c;
-        return EAPDTW_ERR_CUDA;
+        prev = -1;
+        return;
     }
-    *out = c;
-    return EAPDTW_OK;
+    ok = prev == dev || cudaSetDevice(dev) == cudaSuccess;
+    if (!ok) cudaGetLastError();
 }
 
-int32_t eapdtw_ctx_destroy(eapdtw_ctx* c) {
-    if (!c) return EAPDTW_ERR_INVALID_ARG;
-    {
-        std::lock_guard<std::mutex> lk(c->mu);
-        DeviceGuard g(c->device);
-        cudaDeviceSynchronize();
-        free_arena(c);
-        if (c->ev0) cudaEventDestroy(c->ev0);
-        if (c->ev1) cudaEventDestroy(c->ev1);
-        for (RefEntry& r : c->refs) free_ref(r);
-        c->refs.clear();
-        if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
-    }
-    delete c;
-    return EAPDTW_OK;
+DeviceGuard::~DeviceGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
 }
 
-int32_t eapdtw_ref_register(eapdtw_ctx* c, const float* R, int64_t lR, int32_t* ref_id, void* stream) {
-    if (!c || !R || !ref_id || lR < 1) return EAPDTW_ERR_INVALID_ARG;
-    if (lR >= (int64_t(1) << 31)) return EAPDTW_ERR_UNSUPPORTED;
-    std::lock_guard<std::mutex> lk(c->mu);
-    DeviceGuard g(c->device);
-    if (!g.ok) return EAPDTW_ERR_CUDA;
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
-    const int64_t nch = (lR + kChunk - 1) / kChunk;
-    RefEntry r;
-    r.n = lR;
-    int64_t bytes = 0;
-    const bool ok = dalloc(r.R, lR, bytes) && dalloc(r.P1, lR, bytes) && dalloc(r.P2, lR, bytes) &&
-                    dalloc(r.T1, nch, bytes) && dalloc(r.T2, nch, bytes) && dalloc(r.A, nch, bytes);
-    int* bad = nullptr;
-    int64_t bb = 0;
-    auto undo = [&](int32_t rc) {
-        dfree(r.R); dfree(r.P1); dfree(r.P2); dfree(r.T1); dfree(r.T2); dfree(r.A); dfree(bad);
-        return rc;
-    };
-    if (!ok || (c->budget > 0 && c->used + bytes > c->budget)) return undo(EAPDTW_ERR_OUT_OF_MEMORY);
-    if (!dalloc(bad, 1, bb)) return undo(EAPDTW_ERR_OUT_OF_MEMORY);
-    int hbad = 0;
-    if (cudaMemcpyAsync(r.R, R, sizeof(float) * lR, cudaMemcpyDeviceToDevice, st) != cudaSuccess ||
-        cudaMemsetAsync(bad, 0, sizeof(int), st) != cudaSuccess ||
-        launch_ref_prefix(r.R, lR, r.P1, r.P2, r.T1, r.T2, r.A, bad, st) != cudaSuccess ||
-        cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
-        cudaStreamSynchronize(st) != cudaSuccess) {
-        cudaGetLastError();
-        return undo(EAPDTW_ERR_CUDA);
-    }
-    dfree(bad);
-    if (hbad) return undo(EAPDTW_ERR_NAN_INPUT);
-    r.live = true;
-    r.bytes = bytes;
-    r.emax[0] = r.R;
-    r.emin[0] = r.R;
-    c->used += bytes;
-    int id = -1;
-    for (size_t i = 0; i < c->refs.size(); ++i)
-        if (!c->refs[i].live) { id = static_cast<int>(i); break; }
-    if (id < 0) {
-        id = static_cast<int>(c->refs.size());
-        c->refs.push_back(r);
-    } else {
-        c->refs[id] = r;
-    }
-    *ref_id = id;
-    return EAPDTW_OK;
+// Level of the table for envelope radius r: the largest p with 2^p <= 2r + 1.
+int env_level(int r) {
+    int p = 0;
+    while ((2 << p) <= 2 * r + 1) ++p;
+    return p;
 }
-
-int32_t eapdtw_ref_unregister(eapdtw_ctx* c, int32_t ref_id) {
-    if (!c) return EAPDTW_ERR_INVALID_ARG;
-    std::lock_guard<std::mutex> lk(c->mu);
-    if (ref_id < 0 || ref_id >= static_cast<int32_t>(c->refs.size()) || !c->refs[ref_id].live)
-        return EAPDTW_ERR_INVALID_ARG;
-    DeviceGuard g(c->device);
-    cudaDeviceSynchronize();  // no batch may still read it
-    RefEntry& r = c->refs[ref_id];
-    c->used -= r.bytes;
-    free_ref(r);
-    return EAPDTW_OK;
-}
-
-int32_t eapdtw_ref_info(eapdtw_ctx* c, int32_t ref_id, const float** R, int64_t* lR) {
-    if (!c) return EAPDTW_ERR_INVALID_ARG;
-    std::lock_guard<std::mutex> lk(c->mu);
-    if (ref_id < 0 || ref_id >= static_cast<int32_t>(c->refs.size()) || !c->refs[ref_id].live)
-        return EAPDTW_ERR_INVALID_ARG;
-    if (R) *R = c->refs[ref_id].R;
-    if (lR) *lR = c->refs[ref_id].n;
-    return EAPDTW_OK;
-}
-
-int32_t eapdtw_ctx_info(eapdtw_ctx* c, int64_t* out, int32_t nout) {
-    if (!c || !out || nout < 1) return EAPDTW_ERR_INVALID_ARG;
-    std::lock_guard<std::mutex> lk(c->mu);
-    int64_t live = 0;
-    for (const RefEntry& r : c->refs) live += r.live ? 1 : 0;
-    const int64_t v[EAPDTW_CTX_NINFO] = {c->used, c->budget, live, c->arena_bytes, c->batches, c->items_run,
-                                        c->items_rerun, c->exec ? 1 : 0};
-    for (int i = 0; i < nout && i < EAPDTW_CTX_NINFO; ++i) out[i] = v[i];
-    return EAPDTW_OK;
-}
-
-int32_t eapdtw_set_first_tile(eapdtw_ctx* c, int32_t log2_m, int32_t ratio_tenths, int32_t band, int32_t tile) {
-    if (!c || log2_m < 0 || log2_m > 12 || ratio_tenths < 0 || ratio_tenths > 10 || band < 0 || band > 1)
-        return EAPDTW_ERR_INVALID_ARG;
-    if (tile != 0 && tile != 4 && tile != 8 && tile != 16 && tile != 32) return EAPDTW_ERR_INVALID_ARG;
-    std::lock_guard<std::mutex> lk(c->mu);
-    const auto key = std::make_tuple(static_cast<int>(log2_m), static_cast<int>(ratio_tenths), static_cast<int>(band));
-    if (tile == 0) c->tuned.erase(key);
-    else c->tuned[key] = tile;
-    return EAPDTW_OK;
-}
-
-}  // extern "C"
-
-namespace {
 
 // Build the reference's running-extrema table up to level p (blocking).
 int32_t ensure_env(eapdtw_ctx* c, RefEntry& r, int p, cudaStream_t st) {
@@ -560,199 +257,7 @@ int32_t ensure_env(eapdtw_ctx* c, RefEntry& r, int p, cudaStream_t st) {
         r.bytes += bytes;
         r.env_levels = q + 1;
     }
-    return EAPDTW_OK;
-}
-
-// The batched search with the context locked and its device current.
-// ref_len (optional): item i searches only the first ref_len[i] points of its
-// reference (a multiple of the statistics chunk, or the whole reference).
-// graph_ms (optional): device time of the launch sequence.
-int32_t run_batch(eapdtw_ctx* c, const eapdtw_item* items, int32_t n, int32_t kstride, int64_t* out_idx,
-                  double* out_dist, int64_t* counters, void* stream, const int64_t* ref_len, float* graph_ms) {
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
-
-    // ---- host planning: items, query slots, classes, seed samples ----------
-    struct Plan1 {
-        int m, w, level0, slot, cls, scls;
-        bool unc;
-        int64_t n, nw, tiles, ns;
-    };
-    std::vector<Plan1> P(n);
-    std::map<std::tuple<const float*, int, int>, int> slot_of;
-    std::vector<QuerySlot> slots;
-    int64_t qf = 0, samples = 0, sum_nw = 0;
-    for (int i = 0; i < n; ++i) {
-        const eapdtw_item& it = items[i];
-        if (!it.Q || it.lQ < 1 || it.w < 0 || it.k < 1 || it.k > kstride) return EAPDTW_ERR_INVALID_ARG;
-        if (it.ref_id < 0 || it.ref_id >= static_cast<int32_t>(c->refs.size()) || !c->refs[it.ref_id].live)
-            return EAPDTW_ERR_INVALID_ARG;
-        const RefEntry& r = c->refs[it.ref_id];
-        const int64_t rn = ref_len ? std::min(ref_len[i], r.n) : r.n;
-        if (it.lQ > rn) return EAPDTW_ERR_INVALID_ARG;
-        if (it.lQ > kMaxQ) return EAPDTW_ERR_UNSUPPORTED;
-        Plan1& p = P[i];
-        p.n = rn;
-        p.m = static_cast<int>(it.lQ);
-        p.w = static_cast<int>(it.w < p.m ? it.w : p.m);
-        p.unc = p.w >= p.m - 1;
-        p.nw = rn - p.m + 1;
-        p.tiles = (p.nw + 31) / 32;
-        p.ns = p.nw >= 2048 ? std::min<int64_t>(p.nw, kBatchSeedSamples) : 0;
-        p.level0 = first_level(c, p.m, p.w, p.unc);
-        p.cls = p.level0 * 3 + band_mode(p.level0, p.w, p.unc);
-        p.scls = kBatchClasses + (p.m > 32 * 32 ? 3 : 0) + band_mode(3, p.w, p.unc);
-        const auto key = std::make_tuple(it.Q, p.m, p.w);
-        auto f = slot_of.find(key);
-        if (f == slot_of.end()) {
-            QuerySlot q{};
-            q.Q = it.Q;
-            q.m = p.m;
-            q.w = p.w;
-            q.off = static_cast<int>(qf);
-            qf += 5 * static_cast<int64_t>(query_pad(p.m));
-            if (qf >= (int64_t(1) << 31)) return EAPDTW_ERR_UNSUPPORTED;
-            p.slot = static_cast<int>(slots.size());
-            slot_of.emplace(key, p.slot);
-            slots.push_back(q);
-        } else {
-            p.slot = f->second;
-        }
-        samples += p.ns;
-        sum_nw += p.nw;
-    }
-    const int nslots = static_cast<int>(slots.size());
-    // running-extrema levels the items' LB_Keogh EC needs
-    for (int i = 0; i < n; ++i) {
-        if (items[i].no_lb) continue;
-        const int32_t e = ensure_env(c, c->refs[items[i].ref_id], env_level(std::min(P[i].w, P[i].m - 1)), st);
-        if (e != EAPDTW_OK) return e;
-    }
-    int32_t rc = ensure_arena(c, n, nslots, qf, samples, sum_nw + static_cast<int64_t>(kBatchSeedBest) * n);
-    if (rc != EAPDTW_OK) return rc;
-
-    // ---- work tables into the pinned staging buffer ------------------------
-    const Layout& L = c->lay;
-    unsigned char* H = c->htables;
-    int* hdr = reinterpret_cast<int*>(H + L.hdr);
-    hdr[0] = n;
-    hdr[1] = nslots;
-    hdr[2] = kstride;
-    BatchClass* cls = reinterpret_cast<BatchClass*>(H + L.classes);
-    BatchItem* hit = reinterpret_cast<BatchItem*>(H + L.items);
-    int* citems = reinterpret_cast<int*>(H + L.citems);
-    int64_t* cprefix = reinterpret_cast<int64_t*>(H + L.cprefix);
-    int64_t* sprefix = reinterpret_cast<int64_t*>(H + L.sprefix);
-    QuerySlot* hq = reinterpret_cast<QuerySlot*>(H + L.qslots);
-    std::memcpy(hq, slots.data(), sizeof(QuerySlot) * nslots);
-    int cnt[kAllClasses] = {0};
-    for (int i = 0; i < n; ++i) {
-        ++cnt[P[i].cls];
-        if (P[i].ns > 0) ++cnt[P[i].scls];
-    }
-    int off = 0;
-    for (int k = 0; k < kAllClasses; ++k) {
-        cls[k].item_off = off;
-        cls[k].nitems = 0;
-        off += cnt[k];
-    }
-    sprefix[0] = 0;
-    for (int i = 0; i < n; ++i) {
-        const Plan1& p = P[i];
-        const eapdtw_item& it = items[i];
-        const RefEntry& r = c->refs[it.ref_id];
-        BatchItem b{};
-        b.ref = RefView{r.R, p.n, r.P1, r.P2, r.T1, r.T2, r.A};
-        const int mp = query_pad(p.m);
-        const float* base = c->qarena + slots[p.slot].off;
-        b.zq = base;
-        b.uq = base + mp;
-        b.lq = base + 2 * mp;
-        b.zqo = base + 3 * mp;
-        b.ord = reinterpret_cast<const int*>(base + 4 * mp);
-        b.nw = p.nw;
-        b.seed_off = sprefix[i];
-        b.m = p.m;
-        b.w = p.w;
-        b.k = it.k;
-        b.use_lb = it.no_lb ? 0 : 1;
-        b.seed_ns = static_cast<int>(p.ns);
-        b.level0 = p.level0;
-        for (int lv = 0; lv < kBatchLevels; ++lv) {
-            int nxt = -1;
-            if (lv < 3) nxt = band_mode(lv + 1, p.w, p.unc);
-            else if (lv == 3 && p.m > 32 * 32) nxt = band_mode(4, p.w, p.unc);
-            b.band_next[lv] = nxt;
-        }
-        const int er = std::min(p.w, p.m - 1);
-        const int ep = env_level(er);
-        b.ec_w = er;
-        b.ec_d = er - (1 << ep) + 1;
-        b.eu = it.no_lb ? nullptr : r.emax[ep];
-        b.el = it.no_lb ? nullptr : r.emin[ep];
-        hit[i] = b;
-        sprefix[i + 1] = sprefix[i] + p.ns;
-        BatchClass& k = cls[p.cls];
-        const int j = k.nitems++;
-        citems[k.item_off + j] = i;
-        if (p.ns > 0) {
-            BatchClass& sk = cls[p.scls];
-            citems[sk.item_off + sk.nitems++] = i;
-        }
-    }
-    for (int k = 0; k < kBatchClasses; ++k) {
-        int64_t* pre = cprefix + cls[k].item_off + k;
-        pre[0] = 0;
-        for (int j = 0; j < cls[k].nitems; ++j) pre[j + 1] = pre[j] + P[citems[cls[k].item_off + j]].tiles;
-    }
-    auto up = [&](int64_t o, int64_t bytes) {
-        return cudaMemcpyAsync(c->tables + o, H + o, static_cast<size_t>(bytes), cudaMemcpyHostToDevice, st);
-    };
-    CKC(up(L.hdr, 64));
-    CKC(up(L.classes, sizeof(BatchClass) * kAllClasses));
-    CKC(up(L.items, sizeof(BatchItem) * static_cast<int64_t>(n)));
-    CKC(up(L.citems, sizeof(int) * static_cast<int64_t>(off)));
-    CKC(up(L.cprefix, sizeof(int64_t) * static_cast<int64_t>(n + kBatchClasses)));
-    CKC(up(L.sprefix, sizeof(int64_t) * static_cast<int64_t>(n + 1)));
-    CKC(up(L.qslots, sizeof(QuerySlot) * static_cast<int64_t>(nslots)));
-
-    // ---- the launch sequence (a graph replay) ------------------------------
-    rc = ensure_graph(c);
-    if (rc != EAPDTW_OK) return rc;
-    if (graph_ms) CKC(cudaEventRecord(c->ev0, st));
-    CKC(cudaGraphLaunch(c->exec, st));
-    if (graph_ms) CKC(cudaEventRecord(c->ev1, st));
-    const size_t rows = static_cast<size_t>(n) * kstride;
-    CKC(cudaMemcpyAsync(out_idx, c->res_idx, sizeof(int64_t) * rows, cudaMemcpyDeviceToDevice, st));
-    CKC(cudaMemcpyAsync(out_dist, c->res_dist, sizeof(double) * rows, cudaMemcpyDeviceToDevice, st));
-    int* hf = c->h_flags;
-    int* hqb = hf + c->cap_items;
-    unsigned long long* hc = reinterpret_cast<unsigned long long*>(hqb + c->cap_slots + (c->cap_slots & 1));
-    CKC(cudaMemcpyAsync(hf, c->flags, sizeof(int) * n, cudaMemcpyDeviceToHost, st));
-    CKC(cudaMemcpyAsync(hqb, c->qbad, sizeof(int) * nslots, cudaMemcpyDeviceToHost, st));
-    CKC(cudaMemcpyAsync(hc, c->counters(), sizeof(unsigned long long) * kNumCounters, cudaMemcpyDeviceToHost, st));
-    CKC(cudaStreamSynchronize(st));
-    ++c->batches;
-    c->items_run += n;
-    for (int q = 0; q < nslots; ++q)
-        if (hqb[q]) return EAPDTW_ERR_NAN_INPUT;
-    if (graph_ms) CKC(cudaEventElapsedTime(graph_ms, c->ev0, c->ev1));
-    if (counters) {
-        for (int j = 0; j < EAPDTW_NCOUNTERS; ++j) counters[j] = j < 10 ? static_cast<int64_t>(hc[j]) : 0;
-    }
-
-    // ---- items that lost a re-run entry (a list was full): run them alone --
-    for (int i = 0; i < n; ++i) {
-        if (!(hf[i] & 1)) continue;
-        const eapdtw_item& it = items[i];
-        const RefEntry& r = c->refs[it.ref_id];
-        eapdtw_search_opts o{};
-        o.no_lb = it.no_lb;
-        rc = subseq_search_ex(it.Q, it.lQ, r.R, P[i].n, it.w, it.k, &o, out_idx + static_cast<int64_t>(i) * kstride,
-                              out_dist + static_cast<int64_t>(i) * kstride, stream);
-        if (rc != EAPDTW_OK) return rc;
-        ++c->items_rerun;
-    }
-    return EAPDTW_OK;
+    return cudaStreamSynchronize(st) == cudaSuccess ? EAPDTW_OK : EAPDTW_ERR_CUDA;
 }
 
 // Signature of an item for the first-level table.
@@ -764,102 +269,312 @@ std::tuple<int, int, int> signature(int m, int w) {
     return std::make_tuple(lg, tenth, unc ? 0 : 1);
 }
 
-}  // namespace
-
-extern "C" {
-
-int32_t eapdtw_search_batch(eapdtw_ctx* c, const eapdtw_item* items, int32_t n, int32_t kstride,
-                            int64_t* out_idx, double* out_dist, int64_t* counters, void* stream) {
-    if (!c || !items || n < 1 || !out_idx || !out_dist || kstride < 1) return EAPDTW_ERR_INVALID_ARG;
-    if (kstride > EAPDTW_MAX_K) return EAPDTW_ERR_UNSUPPORTED;
-    std::lock_guard<std::mutex> lk(c->mu);
-    DeviceGuard g(c->device);
-    if (!g.ok) return EAPDTW_ERR_CUDA;
-    return run_batch(c, items, n, kstride, out_idx, out_dist, counters, stream, nullptr, nullptr);
+// First level (block width 4 << level) of a (query length, window) pair: the
+// narrowest K whose window of 32 blocks covers the band with margin, 8 (or 4
+// for short queries) when unconstrained, unless the autotuner chose otherwise.
+int first_level(const eapdtw_ctx* c, int m, int w) {
+    const bool unconstrained = w >= m - 1;
+    int K = 32;
+    if (!unconstrained) {
+        for (int k = 4; k <= 32; k *= 2)
+            if ((2 * w + k) / (k + 1) + 3 <= 32) { K = k; break; }
+    } else {
+        K = 8;
+        for (int k = 4; k <= 8; k *= 2)
+            if (32 * k >= m) { K = k; break; }
+    }
+    auto it = c->tuned.find(signature(m, w));
+    if (it != c->tuned.end()) K = it->second;
+    int level = 0;
+    while ((4 << level) < K) ++level;
+    return level;
 }
 
-int32_t eapdtw_autotune(eapdtw_ctx* c, const eapdtw_item* items, int32_t n, int64_t sample_windows, void* stream,
-                        int32_t* n_tuned) {
-    if (!c || !items || n < 1 || sample_windows < 1) return EAPDTW_ERR_INVALID_ARG;
-    std::lock_guard<std::mutex> lk(c->mu);
-    DeviceGuard g(c->device);
-    if (!g.ok) return EAPDTW_ERR_CUDA;
-    // one representative per signature not tuned yet: the item with the longest reference
-    std::map<std::tuple<int, int, int>, int> rep;
-    for (int i = 0; i < n; ++i) {
-        const eapdtw_item& it = items[i];
-        if (!it.Q || it.lQ < 1 || it.lQ > kMaxQ || it.w < 0 || it.k < 1 || it.k > EAPDTW_MAX_K) return EAPDTW_ERR_INVALID_ARG;
-        if (it.ref_id < 0 || it.ref_id >= static_cast<int32_t>(c->refs.size()) || !c->refs[it.ref_id].live)
-            return EAPDTW_ERR_INVALID_ARG;
-        const int m = static_cast<int>(it.lQ);
-        const int w = static_cast<int>(it.w < m ? it.w : m);
-        const auto key = signature(m, w);
-        if (c->tuned.count(key)) continue;
-        auto f = rep.find(key);
-        if (f == rep.end() || c->refs[items[f->second].ref_id].n < c->refs[it.ref_id].n) rep[key] = i;
+int band_mode(int level, int w, bool unconstrained) {
+    const int K = batch_level_K(level);
+    return unconstrained ? 0 : (K <= 2 * w + 2 ? 1 : 2);
+}
+
+void plan_item(const eapdtw_ctx* c, const RefEntry& r, int64_t n_used, int m, int w, int k, bool no_lb,
+               PlannedItem& out) {
+    BatchItem& b = out.b;
+    b = BatchItem{};
+    const bool unc = w >= m - 1;
+    b.ref = RefView{r.R, n_used, r.P1, r.P2, r.T1, r.T2, r.A};
+    b.nw = n_used - m + 1;
+    b.win0 = 0;
+    b.nwin = b.nw;
+    b.m = m;
+    b.w = w;
+    b.k = k;
+    b.use_lb = no_lb ? 0 : 1;
+    b.seed_ns = b.nw >= 2048 ? static_cast<int>(std::min<int64_t>(b.nw, kBatchSeedSamples)) : 0;
+    b.level0 = first_level(c, m, w);
+    for (int lv = 0; lv < kBatchLevels; ++lv) {
+        int nxt = -1;
+        if (lv < 3) nxt = band_mode(lv + 1, w, unc);
+        else if (lv == 3 && m > 32 * 32) nxt = band_mode(4, w, unc);
+        b.band_next[lv] = nxt;
     }
-    int64_t* d_idx = nullptr;
-    double* d_dist = nullptr;
+    const int er = std::min(w, m - 1);
+    const int ep = env_level(er);
+    b.ec_w = er;
+    b.ec_d = er - (1 << ep) + 1;
+    b.eu = no_lb ? nullptr : r.emax[ep];
+    b.el = no_lb ? nullptr : r.emin[ep];
+    b.fresh = 1;
+    out.cls = b.level0 * 3 + band_mode(b.level0, w, unc);
+    out.scls = kBatchClasses + (m > 32 * 32 ? 3 : 0) + band_mode(3, w, unc);
+    out.tiles = (b.nwin + 31) / 32;
+}
+
+void arena_free(eapdtw_ctx* c, Arena& a) {
+    drop_graph(a);
+    dfree(a.tables); dfree(a.qarena); dfree(a.qbad); dfree(a.slots); dfree(a.ub_seed);
+    dfree(a.nbest); dfree(a.best); dfree(a.flags); dfree(a.seed_ed); dfree(a.seed_idx);
+    dfree(a.res_idx); dfree(a.res_dist); dfree(a.rr); dfree(a.small);
+    if (a.htables) cudaFreeHost(a.htables);
+    if (a.hbuf) cudaFreeHost(a.hbuf);
+    if (a.hres_idx) cudaFreeHost(a.hres_idx);
+    if (a.hres_dist) cudaFreeHost(a.hres_dist);
+    a.htables = nullptr;
+    a.hbuf = nullptr;
+    a.hres_idx = nullptr;
+    a.hres_dist = nullptr;
+    c->used -= a.bytes;
+    a.bytes = 0;
+    a.cap_items = a.cap_slots = a.cap_states = 0;
+    a.cap_qf = a.cap_samples = 0;
+    a.rr_cap = 0;
+}
+
+int32_t arena_reserve(eapdtw_ctx* c, Arena& a, int items, int qslots, int states, int64_t qf, int64_t samples,
+                      int64_t rr_want) {
+    const int64_t ci = grow(items, a.cap_items), cs = grow(qslots, a.cap_slots), ct = grow(states, a.cap_states);
+    const int64_t cq = grow(qf, a.cap_qf), cm = grow(samples, a.cap_samples);
+    const int64_t cr = std::max<int64_t>(std::min<int64_t>(grow(rr_want, a.rr_cap), a.rr_cap_max), 1);
+    if (ci == a.cap_items && cs == a.cap_slots && ct == a.cap_states && cq == a.cap_qf && cm == a.cap_samples &&
+        cr <= a.rr_cap && a.tables)
+        return EAPDTW_OK;
+    arena_free(c, a);
+    Layout lay;
+    lay.make(static_cast<int>(ci), static_cast<int>(cs));
     int64_t bytes = 0;
-    if (!dalloc(d_idx, EAPDTW_MAX_K, bytes) || !dalloc(d_dist, EAPDTW_MAX_K, bytes)) {
-        dfree(d_idx);
+    const int64_t rows = ci * EAPDTW_MAX_K;
+    const bool ok = dalloc(a.tables, lay.total, bytes) && dalloc(a.qarena, cq, bytes) && dalloc(a.qbad, cs, bytes) &&
+                    dalloc(a.slots, ct * kBatchSlots, bytes) && dalloc(a.ub_seed, ct, bytes) &&
+                    dalloc(a.nbest, ct, bytes) && dalloc(a.best, ct * kBatchSeedBest, bytes) &&
+                    dalloc(a.flags, ct, bytes) && dalloc(a.seed_ed, cm, bytes) && dalloc(a.seed_idx, cm, bytes) &&
+                    dalloc(a.res_idx, rows, bytes) && dalloc(a.res_dist, rows, bytes) &&
+                    dalloc(a.rr, 6 * cr, bytes) && dalloc(a.small, 1024, bytes);
+    a.bytes = bytes;
+    c->used += bytes;
+    if (!ok || (c->budget > 0 && c->used > c->budget)) {
+        arena_free(c, a);
         return EAPDTW_ERR_OUT_OF_MEMORY;
     }
-    if (!c->ev0 && (cudaEventCreate(&c->ev0) != cudaSuccess || cudaEventCreate(&c->ev1) != cudaSuccess)) {
+    const size_t hb = Arena::al8(sizeof(int) * (ct + cs)) + sizeof(unsigned long long) * 2 * kNumCounters;
+    if (cudaHostAlloc(reinterpret_cast<void**>(&a.htables), lay.total, cudaHostAllocDefault) != cudaSuccess ||
+        cudaHostAlloc(reinterpret_cast<void**>(&a.hbuf), hb, cudaHostAllocDefault) != cudaSuccess ||
+        cudaHostAlloc(reinterpret_cast<void**>(&a.hres_idx), sizeof(int64_t) * rows, cudaHostAllocDefault) !=
+            cudaSuccess ||
+        cudaHostAlloc(reinterpret_cast<void**>(&a.hres_dist), sizeof(double) * rows, cudaHostAllocDefault) !=
+            cudaSuccess) {
         cudaGetLastError();
-        dfree(d_idx);
-        dfree(d_dist);
-        return EAPDTW_ERR_CUDA;
+        arena_free(c, a);
+        return EAPDTW_ERR_OUT_OF_MEMORY;
     }
-    int32_t rc = EAPDTW_OK;
-    int tuned = 0;
-    for (const auto& kv : rep) {
-        eapdtw_item it = items[kv.second];
-        const RefEntry& r = c->refs[it.ref_id];
-        // a prefix of whole statistics chunks holding about sample_windows windows
-        int64_t len = (sample_windows + it.lQ - 1 + kChunk - 1) / kChunk * kChunk;
-        if (len >= r.n) len = r.n;
-        const int m = static_cast<int>(it.lQ);
-        const int w = static_cast<int>(it.w < m ? it.w : m);
-        c->tuned.erase(kv.first);
-        const int base = 4 << first_level(c, m, w, w >= m - 1);
-        int cand[3] = {base, base * 2, base / 2};
-        float best_ms = INFINITY;
-        int best_K = base;
-        for (int K : cand) {
-            if (K < 4 || K > 32) continue;
-            c->tuned[kv.first] = K;
-            float ms = 0.0f, ms2 = 0.0f;
-            rc = run_batch(c, &it, 1, it.k, d_idx, d_dist, nullptr, stream, &len, &ms);   // warm-up
-            if (rc == EAPDTW_OK) rc = run_batch(c, &it, 1, it.k, d_idx, d_dist, nullptr, stream, &len, &ms2);
-            if (rc != EAPDTW_OK) break;
-            ms = std::min(ms, ms2);
-            if (ms < best_ms) { best_ms = ms; best_K = K; }
-        }
-        if (rc != EAPDTW_OK) {
-            c->tuned.erase(kv.first);
-            break;
-        }
-        c->tuned[kv.first] = best_K;
-        ++tuned;
-    }
-    dfree(d_idx);
-    dfree(d_dist);
-    if (n_tuned) *n_tuned = tuned;
-    return rc;
-}
-
-int32_t eapdtw_get_first_tile(eapdtw_ctx* c, int32_t log2_m, int32_t ratio_tenths, int32_t band, int32_t* tile) {
-    if (!c || !tile) return EAPDTW_ERR_INVALID_ARG;
-    std::lock_guard<std::mutex> lk(c->mu);
-    auto f = c->tuned.find(std::make_tuple(static_cast<int>(log2_m), static_cast<int>(ratio_tenths), static_cast<int>(band)));
-    *tile = f == c->tuned.end() ? 0 : f->second;
+    a.lay = lay;
+    a.cap_items = static_cast<int>(ci);
+    a.cap_slots = static_cast<int>(cs);
+    a.cap_states = static_cast<int>(ct);
+    a.cap_qf = cq;
+    a.cap_samples = cm;
+    a.rr_cap = static_cast<int>(cr);
     return EAPDTW_OK;
 }
 
-}  // extern "C"
+int32_t arena_run(Arena& a, std::vector<PlannedItem>& items, const std::vector<QuerySlot>& qslots, int kstride,
+                  cudaStream_t st, bool time_it) {
+    const int n = static_cast<int>(items.size());
+    const int nslots = static_cast<int>(qslots.size());
+    const Layout& L = a.lay;
+    unsigned char* H = a.htables;
+    int* hdr = reinterpret_cast<int*>(H + L.hdr);
+    hdr[0] = n;
+    hdr[1] = nslots;
+    hdr[2] = kstride;
+    BatchClass* cls = reinterpret_cast<BatchClass*>(H + L.classes);
+    BatchItem* hit = reinterpret_cast<BatchItem*>(H + L.items);
+    int* citems = reinterpret_cast<int*>(H + L.citems);
+    int64_t* cprefix = reinterpret_cast<int64_t*>(H + L.cprefix);
+    int64_t* sprefix = reinterpret_cast<int64_t*>(H + L.sprefix);
+    QuerySlot* hq = reinterpret_cast<QuerySlot*>(H + L.qslots);
+    if (nslots) std::memcpy(hq, qslots.data(), sizeof(QuerySlot) * nslots);
+    int cnt[kAllClasses] = {0};
+    for (const PlannedItem& p : items) {
+        ++cnt[p.cls];
+        if (p.scls >= 0 && p.b.seed_ns > 0) ++cnt[p.scls];
+    }
+    int off = 0;
+    for (int k = 0; k < kAllClasses; ++k) {
+        cls[k].item_off = off;
+        cls[k].nitems = 0;
+        off += cnt[k];
+    }
+    sprefix[0] = 0;
+    for (int i = 0; i < n; ++i) {
+        PlannedItem& p = items[i];
+        p.b.seed_off = sprefix[i];
+        hit[i] = p.b;
+        sprefix[i + 1] = sprefix[i] + p.b.seed_ns;
+        BatchClass& k = cls[p.cls];
+        citems[k.item_off + k.nitems++] = i;
+        if (p.scls >= 0 && p.b.seed_ns > 0) {
+            BatchClass& sk = cls[p.scls];
+            citems[sk.item_off + sk.nitems++] = i;
+        }
+    }
+    for (int k = 0; k < kBatchClasses; ++k) {
+        int64_t* pre = cprefix + cls[k].item_off + k;
+        pre[0] = 0;
+        for (int j = 0; j < cls[k].nitems; ++j) pre[j + 1] = pre[j] + items[citems[cls[k].item_off + j]].tiles;
+    }
+    auto up = [&](int64_t o, int64_t bytes) {
+        return cudaMemcpyAsync(a.tables + o, H + o, static_cast<size_t>(bytes), cudaMemcpyHostToDevice, st);
+    };
+    CKC(up(L.hdr, 64));
+    CKC(up(L.classes, sizeof(BatchClass) * kAllClasses));
+    CKC(up(L.items, sizeof(BatchItem) * static_cast<int64_t>(n)));
+    CKC(up(L.citems, sizeof(int) * static_cast<int64_t>(off)));
+    CKC(up(L.cprefix, sizeof(int64_t) * static_cast<int64_t>(n + kBatchClasses)));
+    CKC(up(L.sprefix, sizeof(int64_t) * static_cast<int64_t>(n + 1)));
+    if (nslots) CKC(up(L.qslots, sizeof(QuerySlot) * static_cast<int64_t>(nslots)));
+    const int32_t rc = ensure_graph(a);
+    if (rc != EAPDTW_OK) return rc;
+    if (time_it) {
+        if (!a.ev0 && (cudaEventCreate(&a.ev0) != cudaSuccess || cudaEventCreate(&a.ev1) != cudaSuccess)) {
+            cudaGetLastError();
+            return EAPDTW_ERR_CUDA;
+        }
+        CKC(cudaEventRecord(a.ev0, st));
+    }
+    CKC(cudaGraphLaunch(a.exec, st));
+    if (time_it) CKC(cudaEventRecord(a.ev1, st));
+    CKC(cudaMemcpyAsync(a.hflags(), a.flags, sizeof(int) * a.cap_states, cudaMemcpyDeviceToHost, st));
+    if (nslots) CKC(cudaMemcpyAsync(a.hqbad(), a.qbad, sizeof(int) * nslots, cudaMemcpyDeviceToHost, st));
+    CKC(cudaMemcpyAsync(a.hcounters(), a.counters(), sizeof(unsigned long long) * 2 * kNumCounters,
+                        cudaMemcpyDeviceToHost, st));
+    return EAPDTW_OK;
+}
 
-namespace eapdtw {
+namespace {
+
+// The batched search with the context locked and its device current.
+// ref_len (optional): item i searches only the first ref_len[i] points of its
+// reference (a multiple of the statistics chunk, or the whole reference).
+// graph_ms (optional): device time of the launch sequence.
+int32_t run_batch(eapdtw_ctx* c, const eapdtw_item* items, int32_t n, int32_t kstride, int64_t* out_idx,
+                  double* out_dist, int64_t* counters, void* stream, const int64_t* ref_len, float* graph_ms) {
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    std::vector<PlannedItem> P(n);
+    std::vector<int64_t> nused(n);
+    std::map<std::tuple<const float*, int, int>, int> slot_of;
+    std::vector<QuerySlot> slots;
+    std::vector<int> slot_idx(n);
+    int64_t qf = 0, samples = 0, sum_nw = 0;
+    for (int i = 0; i < n; ++i) {
+        const eapdtw_item& it = items[i];
+        if (!it.Q || it.lQ < 1 || it.w < 0 || it.k < 1 || it.k > kstride) return EAPDTW_ERR_INVALID_ARG;
+        if (it.ref_id < 0 || it.ref_id >= static_cast<int32_t>(c->refs.size()) || !c->refs[it.ref_id].live)
+            return EAPDTW_ERR_INVALID_ARG;
+        const RefEntry& r = c->refs[it.ref_id];
+        const int64_t rn = ref_len ? std::min(ref_len[i], r.n) : r.n;
+        if (it.lQ > rn) return EAPDTW_ERR_INVALID_ARG;
+        if (it.lQ > EAPDTW_MAX_QUERY) return EAPDTW_ERR_UNSUPPORTED;
+        nused[i] = rn;
+        const int m = static_cast<int>(it.lQ);
+        const int w = static_cast<int>(it.w < m ? it.w : m);
+        const auto key = std::make_tuple(it.Q, m, w);
+        auto f = slot_of.find(key);
+        if (f == slot_of.end()) {
+            QuerySlot q{};
+            q.Q = it.Q;
+            q.m = m;
+            q.w = w;
+            q.off = static_cast<int>(qf);
+            qf += 5 * static_cast<int64_t>(query_pad(m));
+            if (qf >= (int64_t(1) << 31)) return EAPDTW_ERR_UNSUPPORTED;
+            slot_idx[i] = static_cast<int>(slots.size());
+            slot_of.emplace(key, slot_idx[i]);
+            slots.push_back(q);
+        } else {
+            slot_idx[i] = f->second;
+        }
+    }
+    // running-extrema levels the items' LB_Keogh EC needs
+    for (int i = 0; i < n; ++i) {
+        if (items[i].no_lb) continue;
+        const int m = static_cast<int>(items[i].lQ);
+        const int w = static_cast<int>(items[i].w < m ? items[i].w : m);
+        const int32_t e = ensure_env(c, c->refs[items[i].ref_id], env_level(std::min(w, m - 1)), st);
+        if (e != EAPDTW_OK) return e;
+    }
+    for (int i = 0; i < n; ++i) {
+        const eapdtw_item& it = items[i];
+        const int m = static_cast<int>(it.lQ);
+        const int w = static_cast<int>(it.w < m ? it.w : m);
+        plan_item(c, c->refs[it.ref_id], nused[i], m, w, it.k, it.no_lb != 0, P[i]);
+        P[i].b.state = i;
+        samples += P[i].b.seed_ns;
+        sum_nw += P[i].b.nw;
+    }
+    const int nslots = static_cast<int>(slots.size());
+    int32_t rc = arena_reserve(c, c->batch, n, nslots, n, qf, samples, sum_nw + static_cast<int64_t>(kBatchSeedBest) * n);
+    if (rc != EAPDTW_OK) return rc;
+    Arena& a = c->batch;
+    for (int i = 0; i < n; ++i) {
+        const int mp = query_pad(P[i].b.m);
+        const float* base = a.qarena + slots[slot_idx[i]].off;
+        P[i].b.zq = base;
+        P[i].b.uq = base + mp;
+        P[i].b.lq = base + 2 * mp;
+        P[i].b.zqo = base + 3 * mp;
+        P[i].b.ord = reinterpret_cast<const int*>(base + 4 * mp);
+    }
+    rc = arena_run(a, P, slots, kstride, st, graph_ms != nullptr);
+    if (rc != EAPDTW_OK) return rc;
+    const size_t rows = static_cast<size_t>(n) * kstride;
+    CKC(cudaMemcpyAsync(out_idx, a.res_idx, sizeof(int64_t) * rows, cudaMemcpyDeviceToDevice, st));
+    CKC(cudaMemcpyAsync(out_dist, a.res_dist, sizeof(double) * rows, cudaMemcpyDeviceToDevice, st));
+    CKC(cudaStreamSynchronize(st));
+    ++c->batches;
+    c->items_run += n;
+    const int* hf = a.hflags();
+    const int* hqb = a.hqbad();
+    const unsigned long long* hc = a.hcounters();
+    for (int q = 0; q < nslots; ++q)
+        if (hqb[q]) return EAPDTW_ERR_NAN_INPUT;
+    if (graph_ms) CKC(cudaEventElapsedTime(graph_ms, a.ev0, a.ev1));
+    if (counters) {
+        for (int j = 0; j < EAPDTW_NCOUNTERS; ++j) counters[j] = j < 10 ? static_cast<int64_t>(hc[j]) : 0;
+    }
+    // items that lost a re-run entry (a list was full): run them alone
+    for (int i = 0; i < n; ++i) {
+        if (!(hf[i] & 1)) continue;
+        const eapdtw_item& it = items[i];
+        const RefEntry& r = c->refs[it.ref_id];
+        eapdtw_search_opts o{};
+        o.no_lb = it.no_lb;
+        rc = subseq_search_ex(it.Q, it.lQ, r.R, nused[i], it.w, it.k, &o, out_idx + static_cast<int64_t>(i) * kstride,
+                              out_dist + static_cast<int64_t>(i) * kstride, stream);
+        if (rc != EAPDTW_OK) return rc;
+        ++c->items_rerun;
+    }
+    return EAPDTW_OK;
+}
+
+}  // namespace
 
 cudaError_t launch_batch_k4(int band, const BatchLaunch& args, int blocks, cudaStream_t s);
 cudaError_t launch_batch_k8(int band, const BatchLaunch& args, int blocks, cudaStream_t s);
@@ -917,3 +632,229 @@ cudaError_t batch_attributes() {
 }
 
 }  // namespace eapdtw
+
+using namespace eapdtw;
+
+extern "C" {
+
+int32_t eapdtw_ctx_create(int32_t device, int64_t mem_budget, eapdtw_ctx** out) {
+    if (!out || mem_budget < 0) return EAPDTW_ERR_INVALID_ARG;
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess) { cudaGetLastError(); return EAPDTW_ERR_CUDA; }
+    if (device < 0 || device >= ndev) return EAPDTW_ERR_INVALID_ARG;
+    eapdtw_ctx* c = new (std::nothrow) eapdtw_ctx;
+    if (!c) return EAPDTW_ERR_OUT_OF_MEMORY;
+    c->device = device;
+    c->budget = mem_budget;
+    if (const char* e = std::getenv("EAPDTW_RERUN_LIST_CAP")) {
+        const long long v = std::atoll(e);
+        if (v >= 1) c->batch.rr_cap_max = v;
+    }
+    *out = c;
+    return EAPDTW_OK;
+}
+
+int32_t eapdtw_ctx_destroy(eapdtw_ctx* c) {
+    if (!c) return EAPDTW_ERR_INVALID_ARG;
+    server_shutdown(c);
+    {
+        std::lock_guard<std::mutex> lk(c->mu);
+        DeviceGuard g(c->device);
+        cudaDeviceSynchronize();
+        arena_free(c, c->batch);
+        if (c->batch.ev0) cudaEventDestroy(c->batch.ev0);
+        if (c->batch.ev1) cudaEventDestroy(c->batch.ev1);
+        if (c->batch.cap_stream) cudaStreamDestroy(c->batch.cap_stream);
+        for (RefEntry& r : c->refs) free_ref(r);
+        c->refs.clear();
+    }
+    delete c;
+    return EAPDTW_OK;
+}
+
+int32_t eapdtw_ref_register(eapdtw_ctx* c, const float* R, int64_t lR, int32_t* ref_id, void* stream) {
+    if (!c || !R || !ref_id || lR < 1) return EAPDTW_ERR_INVALID_ARG;
+    if (lR >= (int64_t(1) << 31)) return EAPDTW_ERR_UNSUPPORTED;
+    std::lock_guard<std::mutex> lk(c->mu);
+    DeviceGuard g(c->device);
+    if (!g.ok) return EAPDTW_ERR_CUDA;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int64_t nch = (lR + kChunk - 1) / kChunk;
+    RefEntry r;
+    r.n = lR;
+    int64_t bytes = 0;
+    const bool ok = dalloc(r.R, lR, bytes) && dalloc(r.P1, lR, bytes) && dalloc(r.P2, lR, bytes) &&
+                    dalloc(r.T1, nch, bytes) && dalloc(r.T2, nch, bytes) && dalloc(r.A, nch, bytes);
+    int* bad = nullptr;
+    int64_t bb = 0;
+    auto undo = [&](int32_t rc) {
+        free_ref(r);
+        dfree(bad);
+        return rc;
+    };
+    if (!ok || (c->budget > 0 && c->used + bytes > c->budget)) return undo(EAPDTW_ERR_OUT_OF_MEMORY);
+    if (!dalloc(bad, 1, bb)) return undo(EAPDTW_ERR_OUT_OF_MEMORY);
+    int hbad = 0;
+    if (cudaMemcpyAsync(r.R, R, sizeof(float) * lR, cudaMemcpyDeviceToDevice, st) != cudaSuccess ||
+        cudaMemsetAsync(bad, 0, sizeof(int), st) != cudaSuccess ||
+        launch_ref_prefix(r.R, lR, r.P1, r.P2, r.T1, r.T2, r.A, bad, st) != cudaSuccess ||
+        cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess) {
+        cudaGetLastError();
+        return undo(EAPDTW_ERR_CUDA);
+    }
+    dfree(bad);
+    if (hbad) return undo(EAPDTW_ERR_NAN_INPUT);
+    r.live = true;
+    r.bytes = bytes;
+    r.emax[0] = r.R;
+    r.emin[0] = r.R;
+    c->used += bytes;
+    int id = -1;
+    for (size_t i = 0; i < c->refs.size(); ++i)
+        if (!c->refs[i].live) { id = static_cast<int>(i); break; }
+    if (id < 0) {
+        id = static_cast<int>(c->refs.size());
+        c->refs.push_back(r);
+    } else {
+        c->refs[id] = r;
+    }
+    *ref_id = id;
+    return EAPDTW_OK;
+}
+
+int32_t eapdtw_ref_unregister(eapdtw_ctx* c, int32_t ref_id) {
+    if (!c) return EAPDTW_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(c->mu);
+    if (ref_id < 0 || ref_id >= static_cast<int32_t>(c->refs.size()) || !c->refs[ref_id].live)
+        return EAPDTW_ERR_INVALID_ARG;
+    if (c->refs[ref_id].users > 0) return EAPDTW_ERR_BUSY;
+    DeviceGuard g(c->device);
+    cudaDeviceSynchronize();  // no batch may still read it
+    RefEntry& r = c->refs[ref_id];
+    c->used -= r.bytes;
+    free_ref(r);
+    return EAPDTW_OK;
+}
+
+int32_t eapdtw_ref_info(eapdtw_ctx* c, int32_t ref_id, const float** R, int64_t* lR) {
+    if (!c) return EAPDTW_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(c->mu);
+    if (ref_id < 0 || ref_id >= static_cast<int32_t>(c->refs.size()) || !c->refs[ref_id].live)
+        return EAPDTW_ERR_INVALID_ARG;
+    if (R) *R = c->refs[ref_id].R;
+    if (lR) *lR = c->refs[ref_id].n;
+    return EAPDTW_OK;
+}
+
+int32_t eapdtw_ctx_info(eapdtw_ctx* c, int64_t* out, int32_t nout) {
+    if (!c || !out || nout < 1) return EAPDTW_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(c->mu);
+    int64_t live = 0;
+    for (const RefEntry& r : c->refs) live += r.live ? 1 : 0;
+    const int64_t v[EAPDTW_CTX_NINFO] = {c->used, c->budget, live, c->batch.bytes, c->batches, c->items_run,
+                                        c->items_rerun, c->batch.exec ? 1 : 0};
+    for (int i = 0; i < nout && i < EAPDTW_CTX_NINFO; ++i) out[i] = v[i];
+    return EAPDTW_OK;
+}
+
+int32_t eapdtw_set_first_tile(eapdtw_ctx* c, int32_t log2_m, int32_t ratio_tenths, int32_t band, int32_t tile) {
+    if (!c || log2_m < 0 || log2_m > 12 || ratio_tenths < 0 || ratio_tenths > 10 || band < 0 || band > 1)
+        return EAPDTW_ERR_INVALID_ARG;
+    if (tile != 0 && tile != 4 && tile != 8 && tile != 16 && tile != 32) return EAPDTW_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(c->mu);
+    const auto key = std::make_tuple(static_cast<int>(log2_m), static_cast<int>(ratio_tenths), static_cast<int>(band));
+    if (tile == 0) c->tuned.erase(key);
+    else c->tuned[key] = tile;
+    return EAPDTW_OK;
+}
+
+int32_t eapdtw_get_first_tile(eapdtw_ctx* c, int32_t log2_m, int32_t ratio_tenths, int32_t band, int32_t* tile) {
+    if (!c || !tile) return EAPDTW_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(c->mu);
+    auto f = c->tuned.find(std::make_tuple(static_cast<int>(log2_m), static_cast<int>(ratio_tenths), static_cast<int>(band)));
+    *tile = f == c->tuned.end() ? 0 : f->second;
+    return EAPDTW_OK;
+}
+
+int32_t eapdtw_search_batch(eapdtw_ctx* c, const eapdtw_item* items, int32_t n, int32_t kstride,
+                            int64_t* out_idx, double* out_dist, int64_t* counters, void* stream) {
+    if (!c || !items || n < 1 || !out_idx || !out_dist || kstride < 1) return EAPDTW_ERR_INVALID_ARG;
+    if (kstride > EAPDTW_MAX_K) return EAPDTW_ERR_UNSUPPORTED;
+    std::lock_guard<std::mutex> lk(c->mu);
+    DeviceGuard g(c->device);
+    if (!g.ok) return EAPDTW_ERR_CUDA;
+    return run_batch(c, items, n, kstride, out_idx, out_dist, counters, stream, nullptr, nullptr);
+}
+
+int32_t eapdtw_autotune(eapdtw_ctx* c, const eapdtw_item* items, int32_t n, int64_t sample_windows, void* stream,
+                        int32_t* n_tuned) {
+    if (!c || !items || n < 1 || sample_windows < 1) return EAPDTW_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(c->mu);
+    DeviceGuard g(c->device);
+    if (!g.ok) return EAPDTW_ERR_CUDA;
+    // one representative per signature not tuned yet: the item with the longest reference
+    std::map<std::tuple<int, int, int>, int> rep;
+    for (int i = 0; i < n; ++i) {
+        const eapdtw_item& it = items[i];
+        if (!it.Q || it.lQ < 1 || it.lQ > EAPDTW_MAX_QUERY || it.w < 0 || it.k < 1 || it.k > EAPDTW_MAX_K)
+            return EAPDTW_ERR_INVALID_ARG;
+        if (it.ref_id < 0 || it.ref_id >= static_cast<int32_t>(c->refs.size()) || !c->refs[it.ref_id].live)
+            return EAPDTW_ERR_INVALID_ARG;
+        const int m = static_cast<int>(it.lQ);
+        const int w = static_cast<int>(it.w < m ? it.w : m);
+        const auto key = signature(m, w);
+        if (c->tuned.count(key)) continue;
+        auto f = rep.find(key);
+        if (f == rep.end() || c->refs[items[f->second].ref_id].n < c->refs[it.ref_id].n) rep[key] = i;
+    }
+    int64_t* d_idx = nullptr;
+    double* d_dist = nullptr;
+    int64_t bytes = 0;
+    if (!dalloc(d_idx, EAPDTW_MAX_K, bytes) || !dalloc(d_dist, EAPDTW_MAX_K, bytes)) {
+        dfree(d_idx);
+        return EAPDTW_ERR_OUT_OF_MEMORY;
+    }
+    int32_t rc = EAPDTW_OK;
+    int tuned = 0;
+    for (const auto& kv : rep) {
+        eapdtw_item it = items[kv.second];
+        const RefEntry& r = c->refs[it.ref_id];
+        // a prefix of whole statistics chunks holding about sample_windows windows
+        int64_t len = (sample_windows + it.lQ - 1 + kChunk - 1) / kChunk * kChunk;
+        if (len >= r.n) len = r.n;
+        const int m = static_cast<int>(it.lQ);
+        const int w = static_cast<int>(it.w < m ? it.w : m);
+        c->tuned.erase(kv.first);
+        const int base = 4 << first_level(c, m, w);
+        const int cand[3] = {base, base * 2, base / 2};
+        float best_ms = INFINITY;
+        int best_K = base;
+        for (int K : cand) {
+            if (K < 4 || K > 32) continue;
+            c->tuned[kv.first] = K;
+            float ms = 0.0f, ms2 = 0.0f;
+            rc = run_batch(c, &it, 1, it.k, d_idx, d_dist, nullptr, stream, &len, &ms);   // warm-up
+            if (rc == EAPDTW_OK) rc = run_batch(c, &it, 1, it.k, d_idx, d_dist, nullptr, stream, &len, &ms2);
+            if (rc != EAPDTW_OK) break;
+            ms = std::min(ms, ms2);
+            if (ms < best_ms) {
+                best_ms = ms;
+                best_K = K;
+            }
+        }
+        if (rc != EAPDTW_OK) {
+            c->tuned.erase(kv.first);
+            break;
+        }
+        c->tuned[kv.first] = best_K;
+        ++tuned;
+    }
+    dfree(d_idx);
+    dfree(d_dist);
+    if (n_tuned) *n_tuned = tuned;
+    return rc;
+}
+
+}  // extern "C"

@@ -415,11 +415,18 @@ __global__ void batch_init_kernel(BatchDev D, int cap_items, unsigned long long*
     const int n = *D.nitems;
     const int64_t tid = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
     const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
-    for (int64_t j = tid; j < static_cast<int64_t>(n) * kBatchSlots; j += stride) D.slots[j] = kEmptyKey;
+    // fresh items start from an empty state; the others keep theirs
+    for (int64_t j = tid; j < static_cast<int64_t>(n) * kBatchSlots; j += stride) {
+        const BatchItem& it = D.items[j / kBatchSlots];
+        if (it.fresh) D.slots[static_cast<int64_t>(it.state) * kBatchSlots + j % kBatchSlots] = kEmptyKey;
+    }
     for (int64_t j = tid; j < n; j += stride) {
-        D.ub_seed[j] = __int_as_float(0x7f800000);
-        D.nbest[j] = 0;
-        D.flags[j] = 0;
+        const BatchItem& it = D.items[j];
+        if (it.fresh) {
+            D.ub_seed[it.state] = __int_as_float(0x7f800000);
+            D.nbest[it.state] = 0;
+        }
+        D.flags[it.state] = 0;
     }
     for (int64_t j = tid; j < *D.nslots; j += stride) D.qbad[j] = 0;
     if (tid < ncounters) counters[tid] = 0;
@@ -464,9 +471,9 @@ __global__ void __launch_bounds__(1024) batch_seed_select_kernel(BatchDev D) {
     for (int i = blockIdx.x; i < n; i += gridDim.x) {
         const BatchItem& it = D.items[i];
         if (it.seed_ns <= 0) continue;  // uniform over the block
-        seed_select_block(D.seed_ed + it.seed_off, D.seed_idx + it.seed_off, it.seed_ns, it.k, D.ub_seed + i,
-                          D.best + static_cast<int64_t>(i) * kBatchSeedBest, kBatchSeedBest, D.nbest + i,
-                          static_cast<long long>(i) << 32);
+        seed_select_block(D.seed_ed + it.seed_off, D.seed_idx + it.seed_off, it.seed_ns, it.k, D.ub_seed + it.state,
+                          D.best + static_cast<int64_t>(it.state) * kBatchSeedBest, kBatchSeedBest,
+                          D.nbest + it.state, static_cast<long long>(i) << 32);
     }
 }
 
@@ -478,7 +485,8 @@ __global__ void batch_finalize_kernel(BatchDev D) {
          g += static_cast<int64_t>(gridDim.x) * blockDim.x) {
         const int i = static_cast<int>(g / ks);
         const int j = static_cast<int>(g % ks);
-        const unsigned long long key = j < D.items[i].k ? D.slots[static_cast<int64_t>(i) * kBatchSlots + j] : kEmptyKey;
+        const BatchItem& it = D.items[i];
+        const unsigned long long key = j < it.k ? D.slots[static_cast<int64_t>(it.state) * kBatchSlots + j] : kEmptyKey;
         if (key == kEmptyKey) {
             D.res_idx[g] = -1;
             D.res_dist[g] = __longlong_as_double(0x7ff0000000000000ll);

@@ -66,3 +66,16 @@ def test_context_argument_errors_need_no_gpu(libpath):
     assert L.eapdtw_ctx_info(None, None, 1) == -1
     # the item struct of the binding has the header's layout
     assert ctypes.sizeof(api.Item) == 40
+
+
+def test_serving_argument_errors_need_no_gpu(libpath):
+    L = api.lib()
+    rid = ctypes.c_int64(0)
+    assert L.eapdtw_serve_start(None, 4, 1 << 16) == -1
+    assert L.eapdtw_serve_stop(None) == -1
+    assert L.eapdtw_serve_submit(None, None, 10, 0, 1, 1, 0, ctypes.byref(rid)) == -1
+    assert L.eapdtw_serve_poll(None, 1, None, None, None, 0) == -1
+    assert L.eapdtw_serve_cancel(None, 1) == -1
+    assert L.eapdtw_serve_stats(None, None, 1) == -1
+    assert api.strerror(-9) == "request cancelled"
+    assert api.strerror(1) == "pending"
