@@ -12,6 +12,14 @@ queries copied from pinned host memory and the results read back every step.
 `--impl reference` times the CPU oracle on a bounded sample of the same
 workload instead.
 
+Two more objects on the same line (rank 0, one GPU): `batched` times the
+batched search (eapdtw_search_batch: one graph-captured launch sequence) and
+the one-query-per-call path on the same sample of the batched mix (queries of
+uneven lengths and windows, each against 8 references); `serving` runs the
+serving loop (continuous batching) against a resident 1e8-point reference,
+first with every request submitted at once, then with Poisson arrivals at half
+that throughput, and reports p50/p99 latency and queries/s.
+
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
 """
 from __future__ import annotations
@@ -157,6 +165,146 @@ def cpu_baseline(n_threads=None):
             "seconds": round(t2 - t0, 2)}
 
 
+# Batched sample: the 1,024-query x 8-reference mix, cut to --batch-queries
+# queries (every query against every reference).
+BATCH_REF_SEED, BATCH_QUERY_SEED = 3, 2
+# Serving: a resident random walk of 1e8 points; requests with m log-uniform in
+# [64, 4096], window ratio uniform in [0, 0.5], k in {1, 5}.
+SERVE_N, SERVE_ARRIVAL_SEED, SERVE_QUERY_SEED = 100_000_000, 4, 5
+
+
+def batched_section(args, dev):
+    """Batched search (one graph-captured launch sequence over all items)
+    against the one-query-per-call path on the same items."""
+    import math
+    import torch
+    from paper_2010_05371_gb300 import api, synth
+    rr = np.random.default_rng(BATCH_REF_SEED)
+    lens = [int(round(math.exp(rr.uniform(math.log(1e5), math.log(1e7))))) for _ in range(8)]
+    refs = [torch.from_numpy(synth.random_walk(n, 100 + j).astype(np.float32)).to(dev)
+            for j, n in enumerate(lens)]
+    rq = np.random.default_rng(BATCH_QUERY_SEED)
+    queries = []
+    for q in range(args.batch_queries):
+        m = int(round(math.exp(rq.uniform(math.log(64), math.log(2048)))))
+        w = int(math.ceil(rq.uniform(0.0, 1.0) * m))
+        ecg = rq.random() < 0.5
+        k = 1 if rq.random() < 0.5 else 5
+        qn = synth.ecg_query(m, 1000 + q) if ecg else synth.random_walk(m, 1000 + q)
+        queries.append((torch.from_numpy(np.asarray(qn, np.float32)).to(dev), w, k))
+    ctx = api.Context(dev.index or 0)
+    ids = [ctx.register(R) for R in refs]
+    items = [(Q, rid, w, k) for (Q, w, k) in queries for rid in ids]
+    windows = sum(refs[rid].numel() - Q.numel() + 1 for (Q, rid, w, k) in items)
+    ctx.search_batch(items, 5)            # warm-up: graph capture, envelope tables
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    bi, bd, cnt = ctx.search_batch(items, 5, return_counters=True)
+    torch.cuda.synchronize()
+    tb = time.perf_counter() - t0
+    big = max(range(len(refs)), key=lambda j: refs[j].numel())
+    api.subseq_search(queries[0][0], refs[big], queries[0][1], 1)   # warm-up of the plain scratch
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    plain = [api.subseq_search(Q, refs[rid], w, k) for (Q, rid, w, k) in items]
+    torch.cuda.synchronize()
+    tp = time.perf_counter() - t0
+    mism = sum(0 if torch.equal(pd, bd[i, :k]) else 1
+               for i, ((Q, rid, w, k), (pi, pd)) in enumerate(zip(items, plain)))
+    ctx.close()
+    return {
+        "config": (f"batched mix: {args.batch_queries} queries (m log-uniform 64-2048, window ratio "
+                   f"uniform 0-1, random walk or ECG-like, k in {{1,5}}, seed {BATCH_QUERY_SEED}) x 8 "
+                   f"random-walk references (n log-uniform 1e5-1e7, seed {BATCH_REF_SEED}), every "
+                   f"query against every reference; a sample of the 1,024-query mix"),
+        "items": len(items), "windows": windows, "timing": "1 timed run after 1 warm-up, host clock, blocking calls",
+        "batched_s": round(tb, 4), "plain_s": round(tp, 4),
+        "batched_windows_per_s": windows / tb, "plain_windows_per_s": windows / tp,
+        "batched_queries_per_s": len(items) / tb, "plain_queries_per_s": len(items) / tp,
+        "speedup": tp / tb, "executed_cells_per_s": cnt["cells"] / tb,
+        "identical_to_plain": f"{len(items) - mism}/{len(items)} items bit-identical distances",
+    }
+
+
+def serving_section(args, dev):
+    """Serving loop against a resident 1e8-point reference: all requests at once
+    (saturated), then Poisson arrivals at half the saturated rate."""
+    import math
+    import torch
+    from paper_2010_05371_gb300 import api, synth
+    n = args.serve_n
+    R = torch.from_numpy(synth.random_walk(n, 0).astype(np.float32)).to(dev)
+    ctx = api.Context(dev.index or 0)
+    rid = ctx.register(R)
+    rq = np.random.default_rng(SERVE_QUERY_SEED)
+
+    def draw(count, base):
+        out = []
+        for i in range(count):
+            m = int(round(math.exp(rq.uniform(math.log(64), math.log(4096)))))
+            w = int(math.ceil(rq.uniform(0.0, 0.5) * m))
+            k = 1 if rq.random() < 0.5 else 5
+            out.append((synth.random_walk(m, base + i).astype(np.float32), w, k))
+        return out
+
+    ctx.serve_start(max_active=args.serve_active, chunk_windows=1 << 22)
+    warm = draw(2, 90_000)
+    for Q, w, k in warm:   # warm-up: graph capture and envelope levels
+        h = ctx.submit(Q, rid, w, k)
+        while ctx.poll(h, k, timeout_ms=1000) is None:
+            pass
+
+    def run(reqs, gaps):
+        handles, t_sub = [], []
+        t0 = time.perf_counter()
+        for (Q, w, k), g in zip(reqs, gaps):
+            if g > 0:
+                time.sleep(g)
+            handles.append(ctx.submit(Q, rid, w, k))
+        lat = []
+        for h, (Q, w, k) in zip(handles, reqs):
+            r = None
+            while r is None:
+                r = ctx.poll(h, k, timeout_ms=1000)
+            lat.append(r[2] / 1e6)
+        wall = time.perf_counter() - t0
+        return {"requests": len(reqs), "wall_s": round(wall, 3), "queries_per_s": len(reqs) / wall,
+                "windows_per_s": sum(n - len(Q) + 1 for Q, w, k in reqs) / wall,
+                "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                "mean_ms": float(np.mean(lat))}
+
+    reqs = draw(args.serve_requests, 10_000)
+    sat = run(reqs, [0.0] * len(reqs))
+    lam = 0.5 * sat["queries_per_s"]
+    ra = np.random.default_rng(SERVE_ARRIVAL_SEED)
+    gaps = list(ra.exponential(1.0 / lam, size=args.serve_requests))
+    gaps[0] = 0.0
+    reqs2 = draw(args.serve_requests, 20_000)
+    poi = run(reqs2, gaps)
+    poi["rate_per_s"] = lam
+    # identity: the two shortest requests of the Poisson run, searched alone by the one-query path
+    same = 0
+    short = sorted(range(len(reqs2)), key=lambda i: len(reqs2[i][0]))[:2]
+    for i in short:
+        Q, w, k = reqs2[i]
+        h = ctx.submit(Q, rid, w, k)
+        r = None
+        while r is None:
+            r = ctx.poll(h, k, timeout_ms=1000)
+        pi, pd = api.subseq_search(torch.from_numpy(Q).to(dev), R, w, k)
+        same += int(np.array_equal(pd.cpu().numpy(), r[1]))
+    st = ctx.serve_stats()
+    ctx.serve_stop()
+    ctx.close()
+    return {
+        "config": (f"serving: resident random walk n={n} (FP32, FP64 chunk sums); requests m log-uniform "
+                   f"64-4096, window ratio uniform 0-0.5, k in {{1,5}} (query seed {SERVE_QUERY_SEED}); "
+                   f"{args.serve_active} state slots, 2^22 windows per request per round"),
+        "saturated": sat, "poisson": poi, "rounds": st["rounds"],
+        "identical_to_plain": f"{same}/{len(short)} requests checked",
+    }
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -191,6 +339,11 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--mode", default="all", choices=["all", "cascade", "nolb"],
                     help="searches per step (profiling aid; the benchmark is 'all')")
+    ap.add_argument("--batch-queries", type=int, default=16,
+                    help="queries of the batched sample (each against 8 references); 0 skips it")
+    ap.add_argument("--serve-requests", type=int, default=24, help="requests per serving run; 0 skips it")
+    ap.add_argument("--serve-active", type=int, default=16, help="state slots of the serving loop")
+    ap.add_argument("--serve-n", type=int, default=SERVE_N, help="serving reference length")
     args = ap.parse_args()
     global SEARCHES
     if args.mode == "cascade":
@@ -347,6 +500,14 @@ def main():
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline()
+    batched = serving = None
+    if rank == 0 and world == 1:
+        del R2, Q2, flush
+        torch.cuda.empty_cache()
+        if args.batch_queries > 0:
+            batched = batched_section(args, dev)
+        if args.serve_requests > 0:
+            serving = serving_section(args, dev)
 
     if rank == 0:
         per_mode = {}
@@ -372,6 +533,8 @@ def main():
             "gpu_launches": launches,
             "clocks": clk,
             "parity": parity,
+            "batched": batched,
+            "serving": serving,
             "wall_s": round(t_wall, 3),
         }
         print(json.dumps(line), flush=True)
