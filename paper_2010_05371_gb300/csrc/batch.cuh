@@ -22,16 +22,25 @@
 
 namespace eapdtw {
 
-constexpr int kBatchLevels = 5;      // K = 4, 8, 16, 32, then the four-window level
+// Levels: K = 4, 8, 16, 32 with one window of 32 blocks, then K = 32 with the
+// columns streamed from shared memory and two windows (queries up to 2048
+// points) or four windows (longer queries).
+constexpr int kBatchLevels = 6;
 constexpr int kBatchClasses = 12;    // first levels 0..3 x band modes 0..2
-constexpr int kSeedClasses = 6;      // seed passes: K = 32 (m <= 1024) or four windows, x band modes
+constexpr int kSeedClasses = 9;      // seed passes at levels 3, 4, 5 x band modes
+constexpr int kRerunBuffers = 3;     // re-run lists of level L live in buffer L % 3
 constexpr int kAllClasses = kBatchClasses + kSeedClasses;
 constexpr int kBatchSeedBest = 32;   // sampled windows per item run through exact DTW
 constexpr int kBatchSeedSamples = 4096;
 constexpr int kBatchSlots = 64;      // k-best slots per item (k <= 64)
-constexpr size_t kWideSmem = sizeof(float) * kWarpsPerBlock * EAPDTW_MAX_QUERY;  // query copies, WIDE
+// Query copies of the widest levels (JW windows of 32 blocks of 32 columns).
+__host__ __device__ constexpr int wide_cols(int JW) { return JW * 1024; }
+__host__ __device__ constexpr size_t wide_smem(int JW) { return sizeof(float) * kWarpsPerBlock * wide_cols(JW); }
 
 __host__ __device__ constexpr int batch_level_K(int level) { return level < 4 ? (4 << level) : 32; }
+__host__ __device__ constexpr int batch_level_windows(int level) { return level == 4 ? 2 : (level == 5 ? 4 : 0); }
+// The widest level a query of m points needs (3 for m <= 1024).
+__host__ __device__ constexpr int batch_last_level(int m) { return m <= 1024 ? 3 : (m <= 2048 ? 4 : 5); }
 
 struct BatchItem {
     RefView ref;
@@ -49,7 +58,8 @@ struct BatchItem {
     int m, w, k, use_lb;
     int seed_ns;         // sampled windows (0: no seed)
     int level0;          // first level
-    int band_next[kBatchLevels];  // band mode of the level that re-runs overflow from level L (-1: none)
+    int next_level[kBatchLevels];  // level that re-runs windows overflowing level L (-1: none)
+    int next_band[kBatchLevels];   // its band mode
     const float* eu;     // sparse-table level of the reference for LB_Keogh EC (see TileCtx)
     const float* el;
     int ec_w, ec_d;
@@ -102,8 +112,8 @@ struct BatchLaunch {
     int scls;                   // seed class whose seed windows this launch runs (-1: none)
     const long long* rr_in;     // re-run entries (item << 32 | window) for this level and band
     const int* rr_in_count;
-    long long* rr_out;          // next level's lists: rr_out + b * rr_cap for band b
-    int* rr_out_count;          // [3]
+    long long* rr;              // every re-run list: rr + (buffer * 3 + band) * rr_cap
+    int* rr_count;              // [kRerunBuffers * 3]
     int rr_cap;
     unsigned long long* work;   // unit counter of this launch
     unsigned long long* counters;
@@ -112,15 +122,15 @@ struct BatchLaunch {
 
 // Persistent batch kernel: the cascade and wavefront of process_tile, the
 // windows read from global memory (items differ in length).  The query is
-// read from global memory too, except at the four-window level (WIDE), which
-// streams the column values at every step: there each warp first copies the
-// item's query into its slot of dynamic shared memory (kMaxQuery floats).
+// read from global memory too, except at the widest level (JW > 1 windows),
+// which streams the column values at every step: there each warp first copies
+// the item's query into its slot of dynamic shared memory (wide_cols(JW) floats).
 // A seed launch (scls >= 0) runs the seed windows of its class, before any
 // tile: their exact distances tighten each item's bound, as the one-query
 // search's seed pass does.  It runs at the widest level, where no live region
 // overflows.
-template <int K, int BAND, bool WIDE>
-__global__ void __launch_bounds__(kWarpsPerBlock * 32, WIDE ? 1 : search_min_blocks(K, BAND))
+template <int K, int BAND, int JW>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32, mode_min_blocks(K, BAND, JW))
 batch_kernel(const BatchLaunch L) {
     __shared__ unsigned long long s_cnt[kNumCounters];
     extern __shared__ __align__(16) float s_q[];
@@ -193,8 +203,8 @@ batch_kernel(const BatchLaunch L) {
         TileCtx C;
         C.ref = it.ref;
         C.zq = it.zq;
-        if (WIDE) {
-            float* q = s_q + warp * EAPDTW_MAX_QUERY;
+        if (JW > 1 && it.m <= wide_cols(JW)) {
+            float* q = s_q + warp * wide_cols(JW);
             __syncwarp();
             for (int j = lane; j < it.m; j += 32) q[j] = it.zq[j];
             __syncwarp();
@@ -219,14 +229,15 @@ batch_kernel(const BatchLaunch L) {
                           0.0f};
         C.nw = it.nw;
         const bool seed = su < nseed;
-        const int bn = seed ? -1 : it.band_next[L.level];
-        C.ovf_out = bn >= 0 ? L.rr_out + static_cast<int64_t>(bn) * L.rr_cap : nullptr;
-        C.ovf_out_count = bn >= 0 ? L.rr_out_count + bn : nullptr;
-        C.ovf_cap = bn >= 0 ? L.rr_cap : 0;
+        const int nx = seed ? -1 : it.next_level[L.level];
+        const int rl = nx >= 0 ? (nx % kRerunBuffers) * 3 + it.next_band[L.level] : -1;
+        C.ovf_out = rl >= 0 ? L.rr + static_cast<int64_t>(rl) * L.rr_cap : nullptr;
+        C.ovf_out_count = rl >= 0 ? L.rr_count + rl : nullptr;
+        C.ovf_cap = rl >= 0 ? L.rr_cap : 0;
         C.tag = static_cast<long long>(item) << 32;
         C.lost = seed ? nullptr : L.D.flags + it.state;   // a seed is only a hint: nothing is lost
         C.dbg = nullptr;
-        process_tile<K, BAND, !WIDE, WIDE, false, 2>(C, nullptr, list, i0, nl, count);
+        process_tile<K, BAND, JW <= 1, JW, false, 2>(C, nullptr, list, i0, nl, count);
     }
     __syncthreads();
     if (threadIdx.x < 10 && s_cnt[threadIdx.x]) atomicAdd(L.counters + threadIdx.x, s_cnt[threadIdx.x]);

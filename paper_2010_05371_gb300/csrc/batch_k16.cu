@@ -7,13 +7,13 @@ namespace eapdtw {
 namespace {
 template <int BAND>
 cudaError_t launch_band(const BatchLaunch& args, int blocks, cudaStream_t s) {
-    batch_kernel<16, BAND, false><<<blocks, kWarpsPerBlock * 32, 0, s>>>(args);
+    batch_kernel<16, BAND, 0><<<blocks, kWarpsPerBlock * 32, 0, s>>>(args);
     return cudaGetLastError();
 }
 template <int BAND>
 int occupancy_blocks() {
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel<16, BAND, false>, kWarpsPerBlock * 32, 0) !=
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel<16, BAND, 0>, kWarpsPerBlock * 32, 0) !=
         cudaSuccess)
         per_sm = 1;
     int dev = 0, sms = 0;
@@ -24,7 +24,7 @@ int occupancy_blocks() {
 template <int BAND>
 cudaError_t attributes() {
     // the windows and the query are read through L1: give it the whole carveout
-    return cudaFuncSetAttribute(batch_kernel<16, BAND, false>, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
+    return cudaFuncSetAttribute(batch_kernel<16, BAND, 0>, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
 }
 }  // namespace
 

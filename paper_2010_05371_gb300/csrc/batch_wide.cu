@@ -1,51 +1,64 @@
-// Instantiations of the batch kernel for the four-window level (K = 32, 4096 columns).
+// Instantiations of the batch kernel for the widest levels: K = 32, the
+// column values streamed from each warp's copy of the query in shared memory,
+// two windows of 32 blocks (level 4, queries up to 2048 points) or four
+// (level 5, longer queries).
 #include "batch.cuh"
 #include "kernels.h"
 
 namespace eapdtw {
 
 namespace {
-template <int BAND>
+template <int BAND, int JW>
 cudaError_t launch_band(const BatchLaunch& args, int blocks, cudaStream_t s) {
-    batch_kernel<32, BAND, true><<<blocks, kWarpsPerBlock * 32, kWideSmem, s>>>(args);
+    batch_kernel<32, BAND, JW><<<blocks, kWarpsPerBlock * 32, wide_smem(JW), s>>>(args);
     return cudaGetLastError();
 }
-template <int BAND>
+template <int BAND, int JW>
 int occupancy_blocks() {
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel<32, BAND, true>, kWarpsPerBlock * 32,
-                                                      kWideSmem) !=
-        cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel<32, BAND, JW>, kWarpsPerBlock * 32,
+                                                      wide_smem(JW)) != cudaSuccess)
         per_sm = 1;
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     return (per_sm > 0 ? per_sm : 1) * sms;
 }
-template <int BAND>
+template <int BAND, int JW>
 cudaError_t attributes() {
-    // the query copies of the eight warps live in dynamic shared memory
-    return cudaFuncSetAttribute(batch_kernel<32, BAND, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                static_cast<int>(kWideSmem));
+    return cudaFuncSetAttribute(batch_kernel<32, BAND, JW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                static_cast<int>(wide_smem(JW)));
+}
+template <int JW>
+cudaError_t launch_j(int band, const BatchLaunch& args, int blocks, cudaStream_t s) {
+    if (band == 0) return launch_band<0, JW>(args, blocks, s);
+    if (band == 1) return launch_band<1, JW>(args, blocks, s);
+    return launch_band<2, JW>(args, blocks, s);
+}
+template <int JW>
+int blocks_j(int band) {
+    if (band == 0) return occupancy_blocks<0, JW>();
+    if (band == 1) return occupancy_blocks<1, JW>();
+    return occupancy_blocks<2, JW>();
+}
+template <int JW>
+cudaError_t attributes_j() {
+    cudaError_t e = attributes<0, JW>();
+    if (e == cudaSuccess) e = attributes<1, JW>();
+    if (e == cudaSuccess) e = attributes<2, JW>();
+    return e;
 }
 }  // namespace
 
-cudaError_t launch_batch_wide(int band, const BatchLaunch& args, int blocks, cudaStream_t s) {
-    if (band == 0) return launch_band<0>(args, blocks, s);
-    if (band == 1) return launch_band<1>(args, blocks, s);
-    return launch_band<2>(args, blocks, s);
+cudaError_t launch_batch_wide(int level, int band, const BatchLaunch& args, int blocks, cudaStream_t s) {
+    return level == 4 ? launch_j<2>(band, args, blocks, s) : launch_j<4>(band, args, blocks, s);
 }
 
-int batch_blocks_wide(int band) {
-    if (band == 0) return occupancy_blocks<0>();
-    if (band == 1) return occupancy_blocks<1>();
-    return occupancy_blocks<2>();
-}
+int batch_blocks_wide(int level, int band) { return level == 4 ? blocks_j<2>(band) : blocks_j<4>(band); }
 
 cudaError_t batch_attributes_wide() {
-    cudaError_t e = attributes<0>();
-    if (e == cudaSuccess) e = attributes<1>();
-    if (e == cudaSuccess) e = attributes<2>();
+    cudaError_t e = attributes_j<2>();
+    if (e == cudaSuccess) e = attributes_j<4>();
     return e;
 }
 

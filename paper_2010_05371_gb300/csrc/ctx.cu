@@ -121,21 +121,21 @@ cudaError_t batch_attrs_once() {
 cudaError_t enqueue_sequence(Arena& a, cudaStream_t s) {
     const BatchDev D = dev_view(a);
     int* rrc = a.rr_counts();
-    cudaError_t e = launch_batch_prep(D, a.cap_items, a.counters(), 2 * kNumCounters, a.work(), kNumWork, rrc, 8,
-                                      EAPDTW_MAX_QUERY, s);
+    cudaError_t e = launch_batch_prep(D, a.cap_items, a.counters(), 2 * kNumCounters, a.work(), kNumWork, rrc,
+                                      3 * kRerunBuffers, EAPDTW_MAX_QUERY, s);
     if (e != cudaSuccess) return e;
-    // seed passes: K = 32 for queries up to 1024 columns, the four-window level beyond
+    // seed passes at each query's widest level, where no live region overflows
     for (int sc = 0; sc < kSeedClasses; ++sc) {
         BatchLaunch L{};
         L.D = D;
-        L.level = sc < 3 ? 3 : 4;
+        L.level = 3 + sc / 3;
         L.band = sc % 3;
         L.cls = -1;
         L.scls = kBatchClasses + sc;
         L.rr_in = nullptr;
         L.rr_in_count = rrc;
-        L.rr_out = a.rr;
-        L.rr_out_count = rrc;
+        L.rr = a.rr;
+        L.rr_count = rrc;
         L.rr_cap = 0;
         L.work = a.work() + kBatchLevels * 3 + sc;
         L.counters = a.seed_counters();
@@ -144,9 +144,16 @@ cudaError_t enqueue_sequence(Arena& a, cudaStream_t s) {
         if (e != cudaSuccess) return e;
     }
     for (int level = 0; level < kBatchLevels; ++level) {
-        const int pin = level & 1, pout = (level + 1) & 1;
-        e = cudaMemsetAsync(rrc + 3 * pout, 0, sizeof(int) * 3, s);
-        if (e != cudaSuccess) return e;
+        // the lists this level fills start empty: level + 1's, and level 5's from level 3
+        if (level <= 3) {
+            e = cudaMemsetAsync(rrc + 3 * ((level + 1) % kRerunBuffers), 0, sizeof(int) * 3, s);
+            if (e != cudaSuccess) return e;
+        }
+        if (level == 3) {
+            e = cudaMemsetAsync(rrc + 3 * (5 % kRerunBuffers), 0, sizeof(int) * 3, s);
+            if (e != cudaSuccess) return e;
+        }
+        const int bin = level % kRerunBuffers;
         for (int band = 0; band < 3; ++band) {
             BatchLaunch L{};
             L.D = D;
@@ -154,10 +161,10 @@ cudaError_t enqueue_sequence(Arena& a, cudaStream_t s) {
             L.band = band;
             L.cls = level < 4 ? level * 3 + band : -1;
             L.scls = -1;
-            L.rr_in = level > 0 ? a.rr + static_cast<int64_t>(3 * pin + band) * a.rr_cap : nullptr;
-            L.rr_in_count = rrc + 3 * pin + band;
-            L.rr_out = a.rr + static_cast<int64_t>(3 * pout) * a.rr_cap;
-            L.rr_out_count = rrc + 3 * pout;
+            L.rr_in = level > 0 ? a.rr + static_cast<int64_t>(3 * bin + band) * a.rr_cap : nullptr;
+            L.rr_in_count = rrc + 3 * bin + band;
+            L.rr = a.rr;
+            L.rr_count = rrc;
             L.rr_cap = a.rr_cap;
             L.work = a.work() + level * 3 + band;
             L.counters = a.counters();
@@ -310,11 +317,11 @@ void plan_item(const eapdtw_ctx* c, const RefEntry& r, int64_t n_used, int m, in
     b.use_lb = no_lb ? 0 : 1;
     b.seed_ns = b.nw >= 2048 ? static_cast<int>(std::min<int64_t>(b.nw, kBatchSeedSamples)) : 0;
     b.level0 = first_level(c, m, w);
+    const int last = batch_last_level(m);
     for (int lv = 0; lv < kBatchLevels; ++lv) {
-        int nxt = -1;
-        if (lv < 3) nxt = band_mode(lv + 1, w, unc);
-        else if (lv == 3 && m > 32 * 32) nxt = band_mode(4, w, unc);
-        b.band_next[lv] = nxt;
+        const int nx = lv < 3 ? lv + 1 : (lv == 3 && last > 3 ? last : -1);
+        b.next_level[lv] = nx;
+        b.next_band[lv] = nx >= 0 ? band_mode(nx, w, unc) : -1;
     }
     const int er = std::min(w, m - 1);
     const int ep = env_level(er);
@@ -324,7 +331,7 @@ void plan_item(const eapdtw_ctx* c, const RefEntry& r, int64_t n_used, int m, in
     b.el = no_lb ? nullptr : r.emin[ep];
     b.fresh = 1;
     out.cls = b.level0 * 3 + band_mode(b.level0, w, unc);
-    out.scls = kBatchClasses + (m > 32 * 32 ? 3 : 0) + band_mode(3, w, unc);
+    out.scls = kBatchClasses + 3 * (last - 3) + band_mode(last, w, unc);
     out.tiles = (b.nwin + 31) / 32;
 }
 
@@ -366,7 +373,7 @@ int32_t arena_reserve(eapdtw_ctx* c, Arena& a, int items, int qslots, int states
                     dalloc(a.nbest, ct, bytes) && dalloc(a.best, ct * kBatchSeedBest, bytes) &&
                     dalloc(a.flags, ct, bytes) && dalloc(a.seed_ed, cm, bytes) && dalloc(a.seed_idx, cm, bytes) &&
                     dalloc(a.res_idx, rows, bytes) && dalloc(a.res_dist, rows, bytes) &&
-                    dalloc(a.rr, 6 * cr, bytes) && dalloc(a.small, 1024, bytes);
+                    dalloc(a.rr, 3 * kRerunBuffers * cr, bytes) && dalloc(a.small, 1024, bytes);
     a.bytes = bytes;
     c->used += bytes;
     if (!ok || (c->budget > 0 && c->used > c->budget)) {
@@ -580,12 +587,12 @@ cudaError_t launch_batch_k4(int band, const BatchLaunch& args, int blocks, cudaS
 cudaError_t launch_batch_k8(int band, const BatchLaunch& args, int blocks, cudaStream_t s);
 cudaError_t launch_batch_k16(int band, const BatchLaunch& args, int blocks, cudaStream_t s);
 cudaError_t launch_batch_k32(int band, const BatchLaunch& args, int blocks, cudaStream_t s);
-cudaError_t launch_batch_wide(int band, const BatchLaunch& args, int blocks, cudaStream_t s);
+cudaError_t launch_batch_wide(int level, int band, const BatchLaunch& args, int blocks, cudaStream_t s);
 int batch_blocks_k4(int band);
 int batch_blocks_k8(int band);
 int batch_blocks_k16(int band);
 int batch_blocks_k32(int band);
-int batch_blocks_wide(int band);
+int batch_blocks_wide(int level, int band);
 cudaError_t batch_attributes_k4();
 cudaError_t batch_attributes_k8();
 cudaError_t batch_attributes_k16();
@@ -598,7 +605,7 @@ cudaError_t launch_batch(int level, int band, const BatchLaunch& args, int block
         case 1: return launch_batch_k8(band, args, blocks, s);
         case 2: return launch_batch_k16(band, args, blocks, s);
         case 3: return launch_batch_k32(band, args, blocks, s);
-        default: return launch_batch_wide(band, args, blocks, s);
+        default: return launch_batch_wide(level, band, args, blocks, s);
     }
 }
 
@@ -616,7 +623,7 @@ int batch_blocks(int level, int band) {
             case 1: v = batch_blocks_k8(band); break;
             case 2: v = batch_blocks_k16(band); break;
             case 3: v = batch_blocks_k32(band); break;
-            default: v = batch_blocks_wide(band); break;
+            default: v = batch_blocks_wide(level, band); break;
         }
     }
     return v;

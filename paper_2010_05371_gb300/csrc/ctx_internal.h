@@ -63,8 +63,8 @@ struct Arena {
     int* seed_idx = nullptr;
     int64_t* res_idx = nullptr;
     double* res_dist = nullptr;
-    long long* rr = nullptr;             // [2][3][rr_cap]
-    unsigned char* small = nullptr;      // rr counts [8] | work [32] | counters [16] | seed counters [16]
+    long long* rr = nullptr;             // [kRerunBuffers][3][rr_cap]
+    unsigned char* small = nullptr;      // rr counts [16] | work [32] | counters [16] | seed counters [16]
     unsigned char* hbuf = nullptr;       // pinned: flags [cap_states] | query flags [cap_slots] | counters
     int64_t* hres_idx = nullptr;         // pinned result rows (serving)
     double* hres_dist = nullptr;

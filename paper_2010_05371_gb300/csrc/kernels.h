@@ -31,7 +31,8 @@ cudaError_t launch_finalize(const unsigned long long* slots, int k, int64_t* out
 // persistent grid (resident blocks per SM x SMs).
 cudaError_t launch_search(int K, int band, bool lb, const SearchArgs& args, int blocks, cudaStream_t s);
 int search_blocks(int K, int band, bool lb, int m);
-// The widest re-run level (K = 32, four windows, 4096 columns).
+// The widest re-run level (K = 32, columns streamed from shared memory; two
+// windows, 2048 columns, for m <= 2048; four windows, 4096 columns, beyond).
 cudaError_t launch_search_wide(int band, const SearchArgs& args, int blocks, cudaStream_t s);
 int search_blocks_wide(int band, int m);
 
@@ -51,8 +52,9 @@ cudaError_t launch_batch_prep(const BatchDev& D, int cap_items, unsigned long lo
                               unsigned long long* work, int nwork, int* rr_counts, int nrr, int m_cap,
                               cudaStream_t s);
 cudaError_t launch_batch_finalize(const BatchDev& D, cudaStream_t s);
-// batch_kernel<K, BAND, WIDE> for one level (0..3: K = 4 << level; 4: the
-// four-window level); batch_attributes must run outside stream capture.
+// batch_kernel for one level (0..3: K = 4 << level, columns in registers;
+// 4, 5: K = 32 with two or four windows, columns streamed from shared
+// memory); batch_attributes must run outside stream capture.
 cudaError_t launch_batch(int level, int band, const BatchLaunch& args, int blocks, cudaStream_t s);
 int batch_blocks(int level, int band);
 cudaError_t batch_attributes();

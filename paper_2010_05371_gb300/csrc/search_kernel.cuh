@@ -107,7 +107,10 @@ struct TileCtx {
 // window's own radius; 2 = a sparse table of running maxima / minima (any
 // radius, two reads per bound; windows within the radius of either end of the
 // reference use a slightly wider envelope, which is still a valid bound).
-template <int K, int BAND, bool LB, bool WIDE, bool STAGE = true, int ECM = 1, typename CountF>
+// JW: 0 = the DP columns' query values held in registers, one window of 32
+// blocks; JW >= 1 = the values streamed from C.zq at every step, JW windows of
+// 32 blocks (fewer registers per thread, more resident warps).
+template <int K, int BAND, bool LB, int JW, bool STAGE = true, int ECM = 1, typename CountF>
 __device__ __forceinline__ void process_tile(const TileCtx& C, float* s_r, bool list_mode, int64_t i0,
                                              int nlanes, CountF count) {
     const int lane = threadIdx.x & 31;
@@ -256,8 +259,8 @@ __device__ __forceinline__ void process_tile(const TileCtx& C, float* s_r, bool 
             if (lane == 0) count(kCntRecheck, 1);
             continue;
         }
-        constexpr int kJ = WIDE ? 4 : dtw_windows(K, BAND);
-        const DtwOut o = dtw_warp<K, BAND, kJ, WIDE>(s_r + off, a_s, cw_s, isd_s, C.zq, m, m, C.w, C.bsf,
+        constexpr int kJ = JW > 0 ? JW : dtw_windows(K, BAND);
+        const DtwOut o = dtw_warp<K, BAND, kJ, (JW > 0)>(s_r + off, a_s, cw_s, isd_s, C.zq, m, m, C.w, C.bsf,
                                                      ub, C.dbg);
         if (lane == 0) {
             count(kCntSteps, static_cast<unsigned long long>(o.steps));
@@ -293,14 +296,19 @@ __device__ __forceinline__ void process_tile(const TileCtx& C, float* s_r, bool 
 __host__ __device__ constexpr int search_min_blocks(int K, int BAND) {
     return dtw_windows(K, BAND) > 1 ? (K <= 4 ? 3 : 2) : (K <= 8 ? 4 : (K <= 16 ? EAPDTW_MINB16 : 2));
 }
+// Same for the streamed-column variants (JW windows).
+__host__ __device__ constexpr int mode_min_blocks(int K, int BAND, int JW) {
+    return JW == 0 ? search_min_blocks(K, BAND) : (JW == 1 ? 3 : (JW == 2 ? 2 : 1));
+}
+
 
 // LB: compile the lower-bound cascade in (true) or out (false, the "nolb"
 // variant and the list-mode re-runs); leaving it out frees registers.
-// WIDE: the last re-run level for the widest live regions: four windows of 32
-// blocks of K columns (4096 columns at K = 32), the column values streamed from
-// shared memory, one resident block per SM.
-template <int K, int BAND, bool LB, bool WIDE = false>
-__global__ void __launch_bounds__(kWarpsPerBlock * 32, WIDE ? 1 : search_min_blocks(K, BAND))
+// JW: 0 for the column values in registers; JW >= 1 streams them from the
+// query in shared memory with JW windows of 32 blocks (the widest re-run level
+// uses four: 4096 columns at K = 32, one resident block per SM).
+template <int K, int BAND, bool LB, int JW = 0>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32, mode_min_blocks(K, BAND, JW))
 search_kernel(const SearchArgs A) {
     extern __shared__ __align__(16) float smem[];
     const int m = A.q.m;
@@ -367,10 +375,10 @@ search_kernel(const SearchArgs A) {
         if (item >= nitems) break;
         if (!list_mode) {
             const int64_t i0 = static_cast<int64_t>(item) * 32;
-            process_tile<K, BAND, LB, WIDE>(C, s_r, false, i0, static_cast<int>(A.nw - i0 < 32 ? A.nw - i0 : 32),
+            process_tile<K, BAND, LB, JW>(C, s_r, false, i0, static_cast<int>(A.nw - i0 < 32 ? A.nw - i0 : 32),
                                             count);
         } else {
-            process_tile<K, BAND, LB, WIDE>(C, s_r, true, A.ovf_in[item] & 0xffffffffll, 1, count);
+            process_tile<K, BAND, LB, JW>(C, s_r, true, A.ovf_in[item] & 0xffffffffll, 1, count);
         }
     }
 
