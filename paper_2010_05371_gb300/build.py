@@ -39,6 +39,25 @@ def sources():
     return sorted(glob.glob(os.path.join(CSRC, "*.cu")))
 
 
+# Sources compiled more than once, with the defines of each unit: each large
+# kernel instantiation gets its own nvcc process (see the files' headers).
+SPLIT_UNITS = {
+    "search_wide.cu": [[]] + [[f"-DEAPDTW_UNIT_JW={j}", f"-DEAPDTW_UNIT_BAND={b}"] for j in (2, 4) for b in (0, 1, 2)],
+    "batch_wide.cu": [[]] + [[f"-DEAPDTW_UNIT_JW={j}", f"-DEAPDTW_UNIT_BAND={b}"] for j in (2, 4) for b in (0, 1, 2)],
+    "pair_kernel.cu": [[], ["-DEAPDTW_UNIT_PAIR_WIDE"]],
+}
+
+
+def units():
+    """(source, extra nvcc flags, object name) of every compile unit."""
+    out = []
+    for src in sources():
+        base = os.path.basename(src)[:-3]
+        for i, defs in enumerate(SPLIT_UNITS.get(os.path.basename(src), [[]])):
+            out.append((src, defs, base + (f".u{i}" if i else "") + ".o"))
+    return out
+
+
 def _inputs():
     files = sources() + glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(CSRC, "*.h"))
     files += glob.glob(os.path.join(INCLUDE, "*.h")) + [os.path.abspath(__file__)]
@@ -63,10 +82,13 @@ def build(force: bool = False, verbose_ptxas: bool = False, jobs: int | None = N
         common += ["-Xptxas", "-v"]
     objs = []
     cmds = []
-    for src in sources():
-        obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
+    for src, defs, name in units():
+        obj = os.path.join(BUILD, name)
         objs.append(obj)
-        cmds.append(common + ["-c", src, "-o", obj])
+        cmds.append(common + defs + ["-c", src, "-o", obj])
+    # the longest units first, so that they do not finish last
+    order = {"search_wide": 0, "batch_wide": 1, "pair_kernel": 2, "search_k32": 3, "search_k16": 4}
+    cmds.sort(key=lambda c: order.get(os.path.basename(c[-1]).split(".")[0], 9))
 
     def run(cmd):
         p = subprocess.run(cmd, capture_output=True, text=True)

@@ -22,26 +22,38 @@ __global__ void __launch_bounds__(32) pair_kernel(const float* __restrict__ rows
     }
 }
 
-namespace {
 template <int K, bool WIDE>
-cudaError_t launch_k(int band, const float* rows, int nr, const float* cols, int nc, int w, float ub,
-                     double* out, cudaStream_t s) {
+cudaError_t launch_pair_k(int band, const float* rows, int nr, const float* cols, int nc, int w, float ub,
+                          double* out, cudaStream_t s) {
     if (band == 0) pair_kernel<K, 0, WIDE><<<1, 32, 0, s>>>(rows, nr, cols, nc, w, ub, out);
     else if (band == 1) pair_kernel<K, 1, WIDE><<<1, 32, 0, s>>>(rows, nr, cols, nc, w, ub, out);
     else pair_kernel<K, 2, WIDE><<<1, 32, 0, s>>>(rows, nr, cols, nc, w, ub, out);
     return cudaGetLastError();
 }
-}  // namespace
+
+// The four-window variant compiles as its own unit (EAPDTW_UNIT_PAIR_WIDE,
+// see build.py); the narrow ones and the dispatcher in the other.
+#ifdef EAPDTW_UNIT_PAIR_WIDE
+
+template cudaError_t launch_pair_k<32, true>(int, const float*, int, const float*, int, int, float, double*,
+                                             cudaStream_t);
+
+#else
+
+extern template cudaError_t launch_pair_k<32, true>(int, const float*, int, const float*, int, int, float,
+                                                    double*, cudaStream_t);
 
 cudaError_t launch_pair(int K, int band, bool wide, const float* rows, int nr, const float* cols, int nc,
                         int w, float ub, double* out, cudaStream_t s) {
-    if (wide) return launch_k<32, true>(band, rows, nr, cols, nc, w, ub, out, s);
+    if (wide) return launch_pair_k<32, true>(band, rows, nr, cols, nc, w, ub, out, s);
     switch (K) {
-        case 4: return launch_k<4, false>(band, rows, nr, cols, nc, w, ub, out, s);
-        case 8: return launch_k<8, false>(band, rows, nr, cols, nc, w, ub, out, s);
-        case 16: return launch_k<16, false>(band, rows, nr, cols, nc, w, ub, out, s);
-        default: return launch_k<32, false>(band, rows, nr, cols, nc, w, ub, out, s);
+        case 4: return launch_pair_k<4, false>(band, rows, nr, cols, nc, w, ub, out, s);
+        case 8: return launch_pair_k<8, false>(band, rows, nr, cols, nc, w, ub, out, s);
+        case 16: return launch_pair_k<16, false>(band, rows, nr, cols, nc, w, ub, out, s);
+        default: return launch_pair_k<32, false>(band, rows, nr, cols, nc, w, ub, out, s);
     }
 }
+
+#endif
 
 }  // namespace eapdtw
