@@ -8,6 +8,11 @@ test-suite, by ``__graft_entry__.smoke()`` and by the CPU-baseline leg of
 
 ``build()`` compiles ``oracle.c`` with gcc into ``oracle/_build``; the other
 functions call it through ctypes and take/return numpy float64 arrays.
+
+The ``o7_*`` functions wrap ``oracle_f32.c``, the FP32-emulating mode: the same
+search with the GPU's FP32/FP64 rounding reproduced operation by operation, so
+that integer outcomes (pruning decisions, completed/abandoned DTWs, indices)
+and FP32 distances compare bit for bit.
 """
 from __future__ import annotations
 
@@ -21,7 +26,10 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "oracle.c")
 _BUILD = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_BUILD, "liboracle.so")
+_SRC_F32 = os.path.join(_HERE, "oracle_f32.c")
+_LIB_F32 = os.path.join(_BUILD, "liboracle_f32.so")
 _lib = None
+_lib_f32 = None
 
 _D = C.POINTER(C.c_double)
 _I64 = C.POINTER(C.c_int64)
@@ -37,19 +45,24 @@ class EapTrace(C.Structure):
     ]
 
 
-def build(force: bool = False) -> str:
-    """Compile oracle.c (gcc, no FMA contraction) and return the .so path."""
+def _compile(src: str, out: str, force: bool) -> str:
     os.makedirs(_BUILD, exist_ok=True)
-    if (not force and os.path.exists(_LIB_PATH)
-            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
-        return _LIB_PATH
-    tmp = _LIB_PATH + f".{os.getpid()}.tmp"
+    if not force and os.path.exists(out) and os.path.getmtime(out) >= os.path.getmtime(src):
+        return out
+    tmp = out + f".{os.getpid()}.tmp"
     subprocess.check_call([
         "gcc", "-O2", "-std=c11", "-D_GNU_SOURCE", "-ffp-contract=off", "-fno-fast-math",
-        "-fPIC", "-shared", "-o", tmp, _SRC, "-lpthread", "-lm",
+        "-fPIC", "-shared", "-o", tmp, src, "-lpthread", "-lm",
     ])
-    os.replace(tmp, _LIB_PATH)
-    return _LIB_PATH
+    os.replace(tmp, out)
+    return out
+
+
+def build(force: bool = False) -> str:
+    """Compile oracle.c and oracle_f32.c (gcc, no FMA contraction); returns
+    the path of the FP64 oracle's .so."""
+    _compile(_SRC_F32, _LIB_F32, force)
+    return _compile(_SRC, _LIB_PATH, force)
 
 
 def _bind(L):
@@ -249,3 +262,128 @@ def search_cascade(Q, R, w: int, k: int = 1, use_lb: bool = True, ub_fixed: floa
     if rc != 0:
         raise ValueError("invalid arguments")
     return idx, dist, dict(zip(COUNTER_NAMES, (int(c) for c in cnt)))
+
+
+# ---------------------------------------------------------------------------
+# FP32-emulating mode (oracle_f32.c)
+# ---------------------------------------------------------------------------
+_F = C.POINTER(C.c_float)
+_I32 = C.POINTER(C.c_int32)
+
+
+def _bind_f32(L):
+    L.o7_rsqrt_rn.restype = C.c_float
+    L.o7_rsqrt_rn.argtypes = [C.c_float]
+    L.o7_ref_prefix.restype = None
+    L.o7_ref_prefix.argtypes = [_F, C.c_int64, _D, _D, _D, _D, _F]
+    L.o7_window_coeffs.restype = None
+    L.o7_window_coeffs.argtypes = [_F, C.c_int64, _D, _D, _D, _D, _F, C.c_int64, C.c_int64, _F, _F, _F]
+    L.o7_query_prep.restype = None
+    L.o7_query_prep.argtypes = [_F, C.c_int64, C.c_int64, _F, _F, _F, _F, _I32]
+    L.o7_dtw_f32.restype = C.c_float
+    L.o7_dtw_f32.argtypes = [_F, _F, C.c_int64, C.c_int64]
+    L.o7_search.restype = C.c_int
+    L.o7_search.argtypes = [_F, C.c_int64, _F, C.c_int64, C.c_int64, C.c_int, C.c_int, C.c_float, C.c_int,
+                            _I64, _I64, _D]
+    return L
+
+
+def lib_f32():
+    global _lib_f32
+    if _lib_f32 is None:
+        build()
+        _lib_f32 = _bind_f32(C.CDLL(_LIB_F32))
+    return _lib_f32
+
+
+def compile_variant_f32(src_text: str, out_dir: str):
+    """A modified copy of oracle_f32.c, bound like lib_f32() (mutation tests)."""
+    os.makedirs(out_dir, exist_ok=True)
+    src = os.path.join(out_dir, "oracle_f32_variant.c")
+    so = os.path.join(out_dir, "liboracle_f32_variant.so")
+    with open(src, "w") as f:
+        f.write(src_text)
+    subprocess.check_call(["gcc", "-O1", "-std=c11", "-D_GNU_SOURCE", "-ffp-contract=off",
+                           "-fPIC", "-shared", "-o", so, src, "-lm"])
+    return _bind_f32(C.CDLL(so))
+
+
+def source_text_f32() -> str:
+    with open(_SRC_F32) as f:
+        return f.read()
+
+
+def _f32(x) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(x, dtype=np.float32))
+
+
+def _pf(a: np.ndarray):
+    return a.ctypes.data_as(_F)
+
+
+O7_COUNTER_NAMES = ("windows", "kim_pruned", "eq_pruned", "ec_pruned", "dtw_abandoned", "dtw_completed")
+
+
+def o7_rsqrt_rn(v: float, L=None) -> float:
+    """Correctly rounded FP32 1/sqrt(v) (v > 0 finite)."""
+    return float((L or lib_f32()).o7_rsqrt_rn(C.c_float(v)))
+
+
+def o7_ref_prefix(R, L=None):
+    """Chunk-anchored prefix sums in the GPU's order: (P1, P2, T1, T2, A)."""
+    R = _f32(R)
+    n = len(R)
+    nch = (n + 4095) // 4096
+    P1, P2 = np.empty(n), np.empty(n)
+    T1, T2 = np.empty(nch), np.empty(nch)
+    A = np.empty(nch, dtype=np.float32)
+    (L or lib_f32()).o7_ref_prefix(_pf(R), n, _p(P1), _p(P2), _p(T1), _p(T2), _pf(A))
+    return P1, P2, T1, T2, A
+
+
+def o7_window_coeffs(R, m: int, windows=None, L=None):
+    """(a, cw, isd) FP32 arrays of the given windows (default: all)."""
+    L = L or lib_f32()
+    R = _f32(R)
+    P1, P2, T1, T2, A = o7_ref_prefix(R, L)
+    idx = range(len(R) - m + 1) if windows is None else windows
+    out = np.empty((len(idx), 3), dtype=np.float32)
+    a, cw, isd = C.c_float(), C.c_float(), C.c_float()
+    for r, i in enumerate(idx):
+        L.o7_window_coeffs(_pf(R), len(R), _p(P1), _p(P2), _p(T1), _p(T2), _pf(A), int(i), int(m),
+                           C.byref(a), C.byref(cw), C.byref(isd))
+        out[r] = (a.value, cw.value, isd.value)
+    return out
+
+
+def o7_query_prep(Q, w: int, L=None):
+    """(zq, uq, lq, zq in LB order, order) as the GPU prepares the query."""
+    Q = _f32(Q)
+    m = len(Q)
+    zq, uq, lq, zqo = (np.empty(m, dtype=np.float32) for _ in range(4))
+    ord_ = np.empty(m, dtype=np.int32)
+    (L or lib_f32()).o7_query_prep(_pf(Q), m, int(w), _pf(zq), _pf(uq), _pf(lq), _pf(zqo),
+                                   ord_.ctypes.data_as(_I32))
+    return zq, uq, lq, zqo, ord_
+
+
+def o7_dtw_f32(z, q, w: int, L=None) -> float:
+    """FP32 DTW of Eq. 1-5 (fma cells) of two equal-length normalised series."""
+    z, q = _f32(z), _f32(q)
+    return float((L or lib_f32()).o7_dtw_f32(_pf(z), _pf(q), len(z), int(w)))
+
+
+def o7_search(Q, R, w: int, k: int = 1, audit_ub: float | None = None, use_lb: bool = True, L=None):
+    """FP32-emulated search: exact top-k (audit_ub None) or the audit cascade under
+    the fixed bound audit_ub.  Returns (idx, dist, counters dict)."""
+    Q, R = _f32(Q), _f32(R)
+    idx = np.empty(k, dtype=np.int64)
+    dist = np.empty(k)
+    cnt = np.zeros(6, dtype=np.int64)
+    audit = audit_ub is not None
+    rc = (L or lib_f32()).o7_search(_pf(Q), len(Q), _pf(R), len(R), int(w), int(k), int(audit),
+                                    C.c_float(float(audit_ub) if audit else 0.0), int(bool(use_lb)),
+                                    cnt.ctypes.data_as(_I64), idx.ctypes.data_as(_I64), _p(dist))
+    if rc != 0:
+        raise ValueError("o7_search: invalid arguments")
+    return idx, dist, dict(zip(O7_COUNTER_NAMES, (int(c) for c in cnt)))

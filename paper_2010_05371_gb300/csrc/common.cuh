@@ -115,6 +115,9 @@ enum Counter : int {
 
 // Window moments from the chunk-anchored sums: mean, population variance and
 // the anchored second moment (the scale of the cancellation error of var).
+// Every FP64 operation of the statistics is an explicit round-to-nearest
+// intrinsic, so that the operation sequence (and an emulation of it) is fixed
+// whatever the compiler's contraction settings.
 __device__ __forceinline__ void window_moments(const RefView& ref, int64_t i, int m, double& mean,
                                                double& var, double& m2anch) {
     const int64_t end = i + m;
@@ -127,19 +130,19 @@ __device__ __forceinline__ void window_moments(const RefView& ref, int64_t i, in
         const int64_t hi = end < cend ? end : cend;
         const double e1 = (hi == cend) ? ref.T1[c] : ref.P1[hi];
         const double e2 = (hi == cend) ? ref.T2[c] : ref.P2[hi];
-        const double p1 = e1 - ref.P1[lo];
-        const double p2 = e2 - ref.P2[lo];
+        const double p1 = __dsub_rn(e1, ref.P1[lo]);
+        const double p2 = __dsub_rn(e2, ref.P2[lo]);
         const double cnt = static_cast<double>(hi - lo);
-        const double dl = static_cast<double>(ref.A[c]) - a0;  // re-anchor to a0
-        s1 += p1 + cnt * dl;
-        s2 += p2 + dl * (2.0 * p1 + cnt * dl);
+        const double dl = __dsub_rn(static_cast<double>(ref.A[c]), a0);  // re-anchor to a0
+        // sum (x - a0) = p1 + cnt dl;  sum (x - a0)^2 = p2 + dl (2 p1 + cnt dl)
+        s1 = __dadd_rn(s1, __fma_rn(cnt, dl, p1));
+        s2 = __dadd_rn(s2, __fma_rn(dl, __fma_rn(cnt, dl, __dmul_rn(2.0, p1)), p2));
         lo = hi;
     }
-    const double inv_m = 1.0 / static_cast<double>(m);
-    const double mu1 = s1 * inv_m;
-    mean = a0 + mu1;
-    m2anch = s2 * inv_m;
-    var = m2anch - mu1 * mu1;
+    const double mu1 = __ddiv_rn(s1, static_cast<double>(m));
+    mean = __dadd_rn(a0, mu1);
+    m2anch = __ddiv_rn(s2, static_cast<double>(m));
+    var = __dsub_rn(m2anch, __dmul_rn(mu1, mu1));
 }
 
 // Window-anchored z coefficients: z(x) = ((x - a) - cw) * isd with a the
@@ -154,21 +157,21 @@ __device__ __forceinline__ void window_coeffs(const RefView& ref, int64_t i, int
     double mean, var, m2a;
     window_moments(ref, i, m, mean, var, m2a);
     a = x[0];
-    if (!(var > 1e-6 * m2a)) {
+    if (!(var > __dmul_rn(1e-6, m2a))) {
         double s = 0.0;
-        for (int p = 0; p < m; ++p) s += static_cast<double>(x[p]);
-        mean = s / static_cast<double>(m);
+        for (int p = 0; p < m; ++p) s = __dadd_rn(s, static_cast<double>(x[p]));
+        mean = __ddiv_rn(s, static_cast<double>(m));
         double v = 0.0;
         for (int p = 0; p < m; ++p) {
-            const double d = static_cast<double>(x[p]) - mean;
-            v += d * d;
+            const double d = __dsub_rn(static_cast<double>(x[p]), mean);
+            v = __fma_rn(d, d, v);
         }
-        var = v / static_cast<double>(m);
+        var = __ddiv_rn(v, static_cast<double>(m));
     }
-    const float var32 = static_cast<float>(var);
+    const float var32 = __double2float_rn(var);
     if (var32 > 0.0f) {
         isd = __frsqrt_rn(var32);
-        cw = static_cast<float>(mean - static_cast<double>(a));
+        cw = __double2float_rn(__dsub_rn(mean, static_cast<double>(a)));
     } else {
         isd = 0.0f;
         cw = 0.0f;

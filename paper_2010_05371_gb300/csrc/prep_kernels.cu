@@ -34,9 +34,9 @@ __global__ void __launch_bounds__(256) ref_prefix_kernel(const float* __restrict
         const int64_t j = tid * kPer + e;
         float x = j < len ? R[base + j] : anchor;
         finite &= isfinite(x);
-        d[e] = static_cast<double>(x) - a;
-        s1 += d[e];
-        s2 += d[e] * d[e];
+        d[e] = __dsub_rn(static_cast<double>(x), a);
+        s1 = __dadd_rn(s1, d[e]);
+        s2 = __fma_rn(d[e], d[e], s2);
     }
     if (!finite) atomicOr(bad, 1);
     // block exclusive scan of (s1, s2)
@@ -47,13 +47,20 @@ __global__ void __launch_bounds__(256) ref_prefix_kernel(const float* __restrict
     for (int o = 1; o < 32; o <<= 1) {
         const double u1 = __shfl_up_sync(0xffffffffu, i1, o);
         const double u2 = __shfl_up_sync(0xffffffffu, i2, o);
-        if (lane >= o) { i1 += u1; i2 += u2; }
+        if (lane >= o) {
+            i1 = __dadd_rn(i1, u1);
+            i2 = __dadd_rn(i2, u2);
+        }
     }
     if (lane == 31) { w1[warp] = i1; w2[warp] = i2; }
     __syncthreads();
     double b1 = 0.0, b2 = 0.0;
-    for (int q = 0; q < warp; ++q) { b1 += w1[q]; b2 += w2[q]; }
-    double r1 = b1 + i1 - s1, r2 = b2 + i2 - s2;  // exclusive prefix of this thread
+    for (int q = 0; q < warp; ++q) {
+        b1 = __dadd_rn(b1, w1[q]);
+        b2 = __dadd_rn(b2, w2[q]);
+    }
+    // exclusive prefix of this thread
+    double r1 = __dsub_rn(__dadd_rn(b1, i1), s1), r2 = __dsub_rn(__dadd_rn(b2, i2), s2);
 #pragma unroll
     for (int e = 0; e < kPer; ++e) {
         const int64_t j = tid * kPer + e;
@@ -61,8 +68,8 @@ __global__ void __launch_bounds__(256) ref_prefix_kernel(const float* __restrict
             P1[base + j] = r1;
             P2[base + j] = r2;
         }
-        r1 += d[e];
-        r2 += d[e] * d[e];
+        r1 = __dadd_rn(r1, d[e]);
+        r2 = __fma_rn(d[e], d[e], r2);
     }
     if (tid == 255) {
         // padded points contribute d = 0
@@ -94,31 +101,34 @@ __device__ void query_prep_block(const float* __restrict__ Q, int m, int w, floa
     if (tid == 0) s_bad = 0;
     __syncthreads();
 
+    // block sum: a thread's strided terms in order, a butterfly over the warp
+    // (every lane ends with the same value), then the warps' sums in order
     auto block_sum = [&](double v) -> double {
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        for (int o = 16; o > 0; o >>= 1) v = __dadd_rn(v, __shfl_xor_sync(0xffffffffu, v, o));
         __syncthreads();
         if ((tid & 31) == 0) red[tid >> 5] = v;
         __syncthreads();
         double t = 0.0;
-        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += red[q];
+        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t = __dadd_rn(t, red[q]);
         return t;
     };
     double s = 0.0;
     for (int j = tid; j < m; j += blockDim.x) {
         const float x = Q[j];
         if (!isfinite(x)) s_bad = 1;
-        s += static_cast<double>(x);
+        s = __dadd_rn(s, static_cast<double>(x));
     }
-    const double mean = block_sum(s) / static_cast<double>(m);
+    const double mean = __ddiv_rn(block_sum(s), static_cast<double>(m));
     double v = 0.0;
     for (int j = tid; j < m; j += blockDim.x) {
-        const double dx = static_cast<double>(Q[j]) - mean;
-        v += dx * dx;
+        const double dx = __dsub_rn(static_cast<double>(Q[j]), mean);
+        v = __fma_rn(dx, dx, v);
     }
-    const double var = block_sum(v) / static_cast<double>(m);
-    const double sd = var > 0.0 ? sqrt(var) : 0.0;
+    const double var = __ddiv_rn(block_sum(v), static_cast<double>(m));
+    const double sd = var > 0.0 ? __dsqrt_rn(var) : 0.0;
     for (int j = tid; j < m; j += blockDim.x) {
-        const float z = sd > 0.0 ? static_cast<float>((static_cast<double>(Q[j]) - mean) / sd) : 0.0f;
+        const float z = sd > 0.0 ? __double2float_rn(__ddiv_rn(__dsub_rn(static_cast<double>(Q[j]), mean), sd))
+                                 : 0.0f;
         s_z[j] = z;
         zq[j] = z;
     }

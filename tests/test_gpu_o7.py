@@ -1,0 +1,70 @@
+"""Bit-exact parity with the FP32-emulating oracle mode: the GPU search's
+distances and indices equal the emulation's exactly, and under a fixed upper
+bound (audit mode) so do its integer outcomes -- the windows pruned by
+LB_Kim, LB_Keogh EQ and LB_Keogh EC, and the EAPrunedDTW runs completed and
+abandoned."""
+import numpy as np
+import pytest
+
+import oracle as O
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+from paper_2010_05371_gb300 import api, synth  # noqa: E402
+
+CASES = [
+    # (series, n, m, w, k, seed)
+    ("walk", 100_000, 128, 13, 1, 0),
+    ("walk", 60_000, 128, 13, 5, 1),
+    ("walk", 30_000, 64, 0, 3, 2),
+    ("walk", 20_000, 200, 200, 2, 3),
+    ("ecg", 40_000, 256, 26, 1, 4),
+    ("walk", 9_000, 600, 150, 1, 5),
+]
+AUDIT_KEYS = ("windows", "kim_pruned", "eq_pruned", "ec_pruned", "dtw_abandoned", "dtw_completed")
+
+
+def inputs(kind, n, m, seed):
+    if kind == "ecg":
+        R, Q = synth.ecg_like(n, seed), synth.ecg_query(m, seed + 50)
+    else:
+        R, Q = synth.random_walk(n, seed), synth.random_walk(m, seed + 50)
+    return np.asarray(R, np.float32), np.asarray(Q, np.float32)
+
+
+def dev(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+@pytest.mark.parametrize("kind,n,m,w,k,seed", CASES)
+def test_results_and_audit_counts_bit_exact(kind, n, m, w, k, seed):
+    R, Q = inputs(kind, n, m, seed)
+    ei, ed, _ = O.o7_search(Q, R, w, k)
+    Rd, Qd = dev(R), dev(Q)
+    gi, gd = api.subseq_search(Qd, Rd, w, k)
+    np.testing.assert_array_equal(gd.cpu().numpy(), ed)
+    np.testing.assert_array_equal(gi.cpu().numpy(), ei)
+    ub = float(np.float32(ed[-1]))
+    for use_lb in (True, False):
+        ai, ad, oc = O.o7_search(Q, R, w, k, audit_ub=ub, use_lb=use_lb)
+        gi2, gd2, gc = api.subseq_search(Qd, Rd, w, k, audit_ub=ub, no_lb=not use_lb, return_counters=True)
+        assert {c: gc[c] for c in AUDIT_KEYS} == oc, (use_lb, gc)
+        np.testing.assert_array_equal(gd2.cpu().numpy(), ad)
+        np.testing.assert_array_equal(gi2.cpu().numpy(), ai)
+
+
+def test_batched_results_bit_exact():
+    items, expect = [], []
+    with api.Context(0) as ctx:
+        refs = {}
+        for kind, n, m, w, k, seed in CASES[:4]:
+            R, Q = inputs(kind, n, m, seed)
+            rid = ctx.register(dev(R))
+            items.append((dev(Q), rid, w, k))
+            expect.append(O.o7_search(Q, R, w, k)[:2])
+        bi, bd = ctx.search_batch(items, 5)
+        bi, bd = bi.cpu().numpy(), bd.cpu().numpy()
+        for j, (ei, ed) in enumerate(expect):
+            k = len(ei)
+            np.testing.assert_array_equal(bd[j, :k], ed)
+            np.testing.assert_array_equal(bi[j, :k], ei)
