@@ -142,7 +142,13 @@ typedef struct {
     int32_t audit;        /* 1: hold ub fixed at ub_fixed for the whole search */
     double ub_fixed;      /* used when audit = 1 */
     int64_t* counters;    /* optional HOST int64[EAPDTW_NCOUNTERS], filled on return */
-    int32_t reserved[8];
+    int32_t tighten;      /* 1: upper-bound tightening with the LB_Keogh EQ terms (the UCR
+                             Suite technique Section 5 keeps): during EAPrunedDTW a cell of
+                             row r is dead once its value plus the terms of rows r+1.. exceed
+                             ub.  Changes the work done, never the result.  First level of the
+                             search, lower bounds on.  Off by default: it saves DTW steps but
+                             costs more time than it saves on the measured workloads. */
+    int32_t reserved[7];
 } eapdtw_search_opts;
 
 /* subseq_search_ex - subseq_search with options (opts may be NULL). */

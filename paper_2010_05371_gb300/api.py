@@ -35,7 +35,8 @@ class SearchOpts(C.Structure):
         ("audit", C.c_int32),
         ("ub_fixed", C.c_double),
         ("counters", C.POINTER(C.c_int64)),
-        ("reserved", C.c_int32 * 8),
+        ("tighten", C.c_int32),
+        ("reserved", C.c_int32 * 7),
     ]
 
 
@@ -199,9 +200,10 @@ def eap_dtw_host(S, T, w: int | None = None, ub: float = math.inf) -> float:
     return out.value
 
 
-def _opts(no_lb, tile, no_seed, audit_ub, counters):
+def _opts(no_lb, tile, no_seed, audit_ub, counters, tighten=False):
     o = SearchOpts()
     o.no_lb = int(bool(no_lb))
+    o.tighten = int(bool(tighten))
     o.tile = int(tile)
     o.no_seed = int(bool(no_seed))
     o.audit = int(audit_ub is not None)
@@ -212,7 +214,7 @@ def _opts(no_lb, tile, no_seed, audit_ub, counters):
 
 def subseq_search(Q, R, w: int, k: int = 1, *, no_lb: bool = False, tile: int = 0,
                   no_seed: bool = False, audit_ub: float | None = None, out=None, stream=None,
-                  return_counters: bool = False):
+                  return_counters: bool = False, tighten: bool = False):
     """k nearest z-normalised subsequences of R to Q under DTW_w (Section 5).
 
     Q, R: CUDA float32 tensors.  Returns (idx int64[k], dist float64[k]) CUDA
@@ -225,7 +227,7 @@ def subseq_search(Q, R, w: int, k: int = 1, *, no_lb: bool = False, tile: int = 
     else:
         idx, dist = out
     cnt = np.zeros(NCOUNTERS, dtype=np.int64)
-    o = _opts(no_lb, tile, no_seed, audit_ub, cnt)
+    o = _opts(no_lb, tile, no_seed, audit_ub, cnt, tighten)
     rc = lib().subseq_search_ex(C.c_void_p(Q.data_ptr()), Q.numel(), C.c_void_p(R.data_ptr()),
                                 R.numel(), int(w), int(k), C.byref(o), C.c_void_p(idx.data_ptr()),
                                 C.c_void_p(dist.data_ptr()), _stream_ptr(stream))

@@ -102,6 +102,9 @@ struct Scratch {
     // overflow lists
     long long* ovf[2] = {nullptr, nullptr};
     int cap_ovf = 0;
+    // upper-bound tightening rows
+    float* cb = nullptr;
+    int64_t cap_cb = 0;
     // host-pointer entry points
     float *dQ = nullptr, *dR = nullptr;
     int64_t cap_dq = 0, cap_dr = 0;
@@ -228,6 +231,20 @@ int32_t search_impl(Scratch& S, const float* Q, int64_t lQ, const float* R, int6
     }
     // a window overflows at most once per level: nw entries always suffice
     const int want_ovf = static_cast<int>(nw);
+    // upper-bound tightening scratch: one row of suffix sums per warp of the largest grid
+    const bool tighten = use_lb && opts && opts->tighten;
+    const int cb_stride = query_pad(m) + 8;
+    if (tighten) {
+        int64_t warps = 0;
+        if (!plan.wide[0]) warps = search_blocks(plan.K[0], plan.band[0], true, m, true) *
+                                   static_cast<int64_t>(search_warps(m));
+        const int64_t want_cb = warps * cb_stride;
+        if (S.cap_cb < want_cb) {
+            S.cap_cb = 0;
+            if (!alloc(S.cb, want_cb)) return EAPDTW_ERR_OUT_OF_MEMORY;
+            S.cap_cb = want_cb;
+        }
+    }
     if (S.cap_ovf < want_ovf) {
         S.cap_ovf = 0;
         if (!alloc(S.ovf[0], want_ovf) || !alloc(S.ovf[1], want_ovf)) return EAPDTW_ERR_OUT_OF_MEMORY;
@@ -261,6 +278,8 @@ int32_t search_impl(Scratch& S, const float* Q, int64_t lQ, const float* R, int6
     a.lb_scale = kLbScale;
     a.counters = S.counters();
     a.dbg = ints + 24;
+    a.cb = tighten ? S.cb : nullptr;
+    a.cb_stride = cb_stride;
 
     if (seed && !audit) {
         const int ns = static_cast<int>(nw < kSeedSamples ? nw : kSeedSamples);
@@ -301,8 +320,9 @@ int32_t search_impl(Scratch& S, const float* Q, int64_t lQ, const float* R, int6
         if (plan.wide[lev]) {
             CK(launch_search_wide(plan.band[lev], la, search_blocks_wide(plan.band[lev], m), st));
         } else {
-            CK(launch_search(plan.K[lev], plan.band[lev], lb, la,
-                             search_blocks(plan.K[lev], plan.band[lev], lb, m), st));
+            const bool tight = tighten && lb;   // first level only
+            CK(launch_search(plan.K[lev], plan.band[lev], lb, la, search_blocks(plan.K[lev], plan.band[lev], lb, m, tight),
+                             st, tight));
         }
         ++launches;
         if (lev == 0) CK(cudaEventRecord(S.ev[3], st));
@@ -509,7 +529,7 @@ int32_t eapdtw_release_scratch(void) {
         release(S->P1); release(S->P2); release(S->T1); release(S->T2); release(S->A);
         release(S->UR); release(S->LR);
         release(S->zq); release(S->uq); release(S->lq); release(S->zqo); release(S->ord);
-        release(S->ovf[0]); release(S->ovf[1]);
+        release(S->ovf[0]); release(S->ovf[1]); release(S->cb);
         release(S->dQ); release(S->dR); release(S->dIdx); release(S->dDist);
         release(S->state); release(S->seed_ed); release(S->seed_idx); release(S->seed_best);
         if (S->host_state) cudaFreeHost(S->host_state);
@@ -524,30 +544,30 @@ int32_t eapdtw_release_scratch(void) {
 
 namespace eapdtw {
 
-cudaError_t launch_search_k4(int band, bool lb, const SearchArgs& args, int blocks, cudaStream_t s);
-cudaError_t launch_search_k8(int band, bool lb, const SearchArgs& args, int blocks, cudaStream_t s);
-cudaError_t launch_search_k16(int band, bool lb, const SearchArgs& args, int blocks, cudaStream_t s);
-cudaError_t launch_search_k32(int band, bool lb, const SearchArgs& args, int blocks, cudaStream_t s);
-int search_blocks_k4(int band, bool lb, int m);
-int search_blocks_k8(int band, bool lb, int m);
-int search_blocks_k16(int band, bool lb, int m);
-int search_blocks_k32(int band, bool lb, int m);
+cudaError_t launch_search_k4(int band, bool lb, const SearchArgs& args, int blocks, cudaStream_t s, bool tight);
+cudaError_t launch_search_k8(int band, bool lb, const SearchArgs& args, int blocks, cudaStream_t s, bool tight);
+cudaError_t launch_search_k16(int band, bool lb, const SearchArgs& args, int blocks, cudaStream_t s, bool tight);
+cudaError_t launch_search_k32(int band, bool lb, const SearchArgs& args, int blocks, cudaStream_t s, bool tight);
+int search_blocks_k4(int band, bool lb, int m, bool tight);
+int search_blocks_k8(int band, bool lb, int m, bool tight);
+int search_blocks_k16(int band, bool lb, int m, bool tight);
+int search_blocks_k32(int band, bool lb, int m, bool tight);
 
-cudaError_t launch_search(int K, int band, bool lb, const SearchArgs& args, int blocks, cudaStream_t s) {
+cudaError_t launch_search(int K, int band, bool lb, const SearchArgs& args, int blocks, cudaStream_t s, bool tight) {
     switch (K) {
-        case 4: return launch_search_k4(band, lb, args, blocks, s);
-        case 8: return launch_search_k8(band, lb, args, blocks, s);
-        case 16: return launch_search_k16(band, lb, args, blocks, s);
-        default: return launch_search_k32(band, lb, args, blocks, s);
+        case 4: return launch_search_k4(band, lb, args, blocks, s, tight);
+        case 8: return launch_search_k8(band, lb, args, blocks, s, tight);
+        case 16: return launch_search_k16(band, lb, args, blocks, s, tight);
+        default: return launch_search_k32(band, lb, args, blocks, s, tight);
     }
 }
 
-int search_blocks(int K, int band, bool lb, int m) {
+int search_blocks(int K, int band, bool lb, int m, bool tight) {
     switch (K) {
-        case 4: return search_blocks_k4(band, lb, m);
-        case 8: return search_blocks_k8(band, lb, m);
-        case 16: return search_blocks_k16(band, lb, m);
-        default: return search_blocks_k32(band, lb, m);
+        case 4: return search_blocks_k4(band, lb, m, tight);
+        case 8: return search_blocks_k8(band, lb, m, tight);
+        case 16: return search_blocks_k16(band, lb, m, tight);
+        default: return search_blocks_k32(band, lb, m, tight);
     }
 }
 

@@ -235,6 +235,7 @@ batch_kernel(const BatchLaunch L) {
         C.ovf_out_count = rl >= 0 ? L.rr_count + rl : nullptr;
         C.ovf_cap = rl >= 0 ? L.rr_cap : 0;
         C.tag = static_cast<long long>(item) << 32;
+        C.cbw = nullptr;
         C.lost = seed ? nullptr : L.D.flags + it.state;   // a seed is only a hint: nothing is lost
         C.dbg = nullptr;
         process_tile<K, BAND, JW <= 1, JW, false, 2>(C, nullptr, list, i0, nl, count);

@@ -33,6 +33,13 @@
 //  * Early abandoning (border collision / full discard line).  When every
 //    block of the window is dead at two consecutive steps, every later cell
 //    has dead inputs only: the result is +inf.
+//  * Upper bound tightening (optional, the UCR Suite's use of LB_Keogh that
+//    Section 5 keeps).  Every warping path visits every row, and a row's cells
+//    cost at least that row's LB_Keogh EQ term, so a cell of row r whose value
+//    plus the terms of rows r+1..nr exceeds ub is dead too.  The threshold
+//    rises with the row, and the retirement and abandon arguments hold with it:
+//    a cell derived from dead cells of row r pays at least the terms of the
+//    rows in between, so it stays above its own row's threshold.
 //  * Band.  Only two cells per row must be forced to +inf: the one just left
 //    of the band (it is the left neighbour of the first band cell) and the one
 //    just right of it (it is the top neighbour of the next row's last band
@@ -84,11 +91,12 @@ __device__ __forceinline__ float f_nan() { return __int_as_float(0x7fffffff); }
 // CS: read the column values from `cols` at every step instead of holding them
 // in registers (for the widest windows, whose registers would not fit).
 // All 32 lanes call it with identical arguments.
-template <int K, int BAND, int J = 1, bool CS = false>
+// TIGHT: upper-bound tightening with cb (see thr below); compiled out otherwise.
+template <int K, int BAND, int J = 1, bool CS = false, bool TIGHT = false>
 __device__ __forceinline__ DtwOut dtw_warp(const float* __restrict__ rows, float a, float cw,
                                            float isd, const float* __restrict__ cols, int nr,
                                            int nc, int w, const BestSoFar bsf, float ub,
-                                           int* dbg = nullptr) {
+                                           int* dbg = nullptr, const float* __restrict__ cb = nullptr) {
     static_assert(K % 4 == 0, "K must be a multiple of 4");
     static_assert(J >= 1 && J <= 4, "1 to 4 windows");
     (void)dbg;
@@ -194,6 +202,17 @@ __device__ __forceinline__ DtwOut dtw_warp(const float* __restrict__ rows, float
         for (int k = 1; k < K; ++k) bmin = fminf(bmin, prv[j][k]);
         return bmin;
     };
+    // Death threshold of window j's block at step `step` (its row r = step - block).
+    // Without tightening: ub.  With it (cb[r] = a lower bound of the cost of rows r+1..nr,
+    // the suffix sums of the window's LB_Keogh EQ terms): a cell of row r is dead
+    // when even the cheapest completion exceeds ub, v > ub (1 + 1e-4) - cb[r]
+    // (the margin absorbs FP32 rounding of v and cb); never looser than ub.
+    auto thr = [&](int j, int step) -> float {
+        if (!TIGHT) return ub;
+        int r = step - (B0 + 32 * j + lane);
+        r = r < 0 ? 0 : (r > nr ? nr : r);
+        return fminf(ub, __fsub_rn(__fmul_rn(ub, 1.0001f), cb[r]));
+    };
     // Border / abandon checks after step t (t a multiple of kCheckEvery);
     // dead_a holds the dead lanes of the step before.  Returns true when the
     // candidate is finished (abandoned or overflowed).
@@ -209,7 +228,7 @@ __device__ __forceinline__ DtwOut dtw_warp(const float* __restrict__ rows, float
         unsigned db[J];
 #pragma unroll
         for (int j = 0; j < J; ++j)
-            db[j] = (j < jact) ? __ballot_sync(kFull, !(bmin_b[j] <= ub)) : kFull;
+            db[j] = (j < jact) ? __ballot_sync(kFull, !(bmin_b[j] <= thr(j, t))) : kFull;
         // Overflow: the last active window passed an alive value beyond itself.
         float om = omin[0];
 #pragma unroll
@@ -313,7 +332,7 @@ __device__ __forceinline__ DtwOut dtw_warp(const float* __restrict__ rows, float
             t += kCheckEvery;
 #pragma unroll
             for (int j = 0; j < J; ++j)
-                dead_a[j] = (j < jact) ? __ballot_sync(kFull, !(bmin_a[j] <= ub)) : kFull;
+                dead_a[j] = (j < jact) ? __ballot_sync(kFull, !(bmin_a[j] <= thr(j, t - 1))) : kFull;
             if (check(bmin_b, t)) break;
             continue;
         }
@@ -362,7 +381,7 @@ __device__ __forceinline__ DtwOut dtw_warp(const float* __restrict__ rows, float
         if (phase == kCheckEvery - 1) {
 #pragma unroll
             for (int j = 0; j < J; ++j)
-                dead_a[j] = (j < jact) ? __ballot_sync(kFull, !(bmin[j] <= ub)) : kFull;
+                dead_a[j] = (j < jact) ? __ballot_sync(kFull, !(bmin[j] <= thr(j, t))) : kFull;
         } else if (phase == 0) {
             if (check(bmin, t)) break;
         }

@@ -29,8 +29,10 @@ cudaError_t launch_finalize(const unsigned long long* slots, int k, int64_t* out
 // search_kernel<K, BAND, LB> for K in {4, 8, 16, 32}, BAND in {0, 1, 2} and
 // LB in {false, true}; one translation unit per K.  search_blocks gives the
 // persistent grid (resident blocks per SM x SMs).
-cudaError_t launch_search(int K, int band, bool lb, const SearchArgs& args, int blocks, cudaStream_t s);
-int search_blocks(int K, int band, bool lb, int m);
+// tight: the first-level variant with upper-bound tightening (lb only).
+cudaError_t launch_search(int K, int band, bool lb, const SearchArgs& args, int blocks, cudaStream_t s,
+                          bool tight = false);
+int search_blocks(int K, int band, bool lb, int m, bool tight = false);
 // The widest re-run level (K = 32, columns streamed from shared memory; two
 // windows, 2048 columns, for m <= 2048; four windows, 4096 columns, beyond).
 cudaError_t launch_search_wide(int band, const SearchArgs& args, int blocks, cudaStream_t s);

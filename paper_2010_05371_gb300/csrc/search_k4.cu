@@ -1,27 +1,28 @@
-// Instantiations of the search kernel for K = 4 DP cells per lane.
+// Instantiations of the search kernel for K = 4 DP cells per lane: band modes
+// 0-2, with and without the lower bounds, and the first-level variants with
+// upper-bound tightening.
 #include "kernels.h"
 #include "search_kernel.cuh"
 
 namespace eapdtw {
 
-
 namespace {
-template <int BAND, bool LB>
+template <int BAND, bool LB, bool TIGHT>
 cudaError_t launch_band(const SearchArgs& args, int blocks, cudaStream_t s) {
     const size_t sm = search_smem_bytes(args.q.m);
-    cudaError_t e = cudaFuncSetAttribute(search_kernel<4, BAND, LB>,
+    cudaError_t e = cudaFuncSetAttribute(search_kernel<4, BAND, LB, 0, TIGHT>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(sm));
     if (e != cudaSuccess) return e;
-    search_kernel<4, BAND, LB><<<blocks, search_warps(args.q.m) * 32, sm, s>>>(args);
+    search_kernel<4, BAND, LB, 0, TIGHT><<<blocks, search_warps(args.q.m) * 32, sm, s>>>(args);
     return cudaGetLastError();
 }
-template <int BAND, bool LB>
+template <int BAND, bool LB, bool TIGHT>
 int occupancy_blocks(int m) {
     const size_t sm = search_smem_bytes(m);
-    cudaFuncSetAttribute(search_kernel<4, BAND, LB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(search_kernel<4, BAND, LB, 0, TIGHT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          static_cast<int>(sm));
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, search_kernel<4, BAND, LB>,
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, search_kernel<4, BAND, LB, 0, TIGHT>,
                                                       search_warps(m) * 32, sm) != cudaSuccess)
         per_sm = 1;
     int dev = 0, sms = 0;
@@ -29,28 +30,28 @@ int occupancy_blocks(int m) {
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     return (per_sm > 0 ? per_sm : 1) * sms;
 }
+template <bool LB, bool TIGHT>
+cudaError_t launch_lb(int band, const SearchArgs& args, int blocks, cudaStream_t s) {
+    if (band == 0) return launch_band<0, LB, TIGHT>(args, blocks, s);
+    if (band == 1) return launch_band<1, LB, TIGHT>(args, blocks, s);
+    return launch_band<2, LB, TIGHT>(args, blocks, s);
+}
+template <bool LB, bool TIGHT>
+int blocks_lb(int band, int m) {
+    if (band == 0) return occupancy_blocks<0, LB, TIGHT>(m);
+    if (band == 1) return occupancy_blocks<1, LB, TIGHT>(m);
+    return occupancy_blocks<2, LB, TIGHT>(m);
+}
 }  // namespace
 
-cudaError_t launch_search_k4(int band, bool lb, const SearchArgs& args, int blocks, cudaStream_t s) {
-    if (lb) {
-        if (band == 0) return launch_band<0, true>(args, blocks, s);
-        if (band == 1) return launch_band<1, true>(args, blocks, s);
-        return launch_band<2, true>(args, blocks, s);
-    }
-    if (band == 0) return launch_band<0, false>(args, blocks, s);
-    if (band == 1) return launch_band<1, false>(args, blocks, s);
-    return launch_band<2, false>(args, blocks, s);
+cudaError_t launch_search_k4(int band, bool lb, const SearchArgs& args, int blocks, cudaStream_t s, bool tight) {
+    if (lb) return tight ? launch_lb<true, true>(band, args, blocks, s) : launch_lb<true, false>(band, args, blocks, s);
+    return launch_lb<false, false>(band, args, blocks, s);
 }
 
-int search_blocks_k4(int band, bool lb, int m) {
-    if (lb) {
-        if (band == 0) return occupancy_blocks<0, true>(m);
-        if (band == 1) return occupancy_blocks<1, true>(m);
-        return occupancy_blocks<2, true>(m);
-    }
-    if (band == 0) return occupancy_blocks<0, false>(m);
-    if (band == 1) return occupancy_blocks<1, false>(m);
-    return occupancy_blocks<2, false>(m);
+int search_blocks_k4(int band, bool lb, int m, bool tight) {
+    if (lb) return tight ? blocks_lb<true, true>(band, m) : blocks_lb<true, false>(band, m);
+    return blocks_lb<false, false>(band, m);
 }
 
 }  // namespace eapdtw

@@ -44,6 +44,8 @@ struct SearchArgs {
     const long long* ovf_in;  // list mode input
     const int* ovf_in_count;
     int ovf_in_cap;           // entries beyond the capacity were dropped by the producer
+    float* cb;                // upper-bound tightening scratch: cb_stride floats per warp of the grid, or nullptr
+    int cb_stride;
     int* dbg;                 // device self-check record (EAPDTW_DEVICE_CHECKS builds only)
 };
 
@@ -93,8 +95,48 @@ struct TileCtx {
     int ovf_cap;
     long long tag;        // high bits of the overflow entries (batch item << 32)
     int* lost;            // set to 1 when an overflow entry did not fit the list (or nullptr)
+    float* cbw;           // this warp's scratch for upper-bound tightening (>= m + 1 floats), or nullptr
     int* dbg;
 };
+
+// Suffix sums of a window's LB_Keogh EQ terms by position, cb[r] = sum of the
+// terms of rows r+1..m (1-based; cb[m] = 0), into the warp's scratch: a row
+// costs at least its term on any warping path, so cb[r] bounds the cost still
+// to come after row r (upper bound tightening, see dtw_wavefront.cuh).
+__device__ __forceinline__ void tightening_terms(const TileCtx& C, const float* x, float a, float cw, float isd) {
+    const int lane = threadIdx.x & 31;
+    const int m = C.m;
+    float* cb = C.cbw;
+    for (int p = lane; p < m; p += 32) {
+        const int j = C.ord[p];
+        const float z = znorm1(x[j], a, cw, isd);
+        const float e = fmaxf(fmaxf(__fsub_rn(z, C.uq[p]), __fsub_rn(C.lq[p], z)), 0.0f);
+        cb[j] = __fmul_rn(e, e);
+    }
+    __syncwarp();
+    // lane l owns positions [l S, (l + 1) S): suffix sums inside, then the
+    // totals of the lanes to its right
+    const int S = (m + 31) >> 5;
+    const int lo = lane * S;
+    const int hi = lo + S < m ? lo + S : m;
+    float acc = 0.0f;
+    for (int j = hi - 1; j >= lo; --j) {
+        acc = __fadd_rn(acc, cb[j]);
+        cb[j] = acc;
+    }
+    float v = acc;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const float u = __shfl_down_sync(kFull, v, o);
+        if (lane + o < 32) v = __fadd_rn(v, u);
+    }
+    float add = __shfl_down_sync(kFull, v, 1);
+    if (lane == 31) add = 0.0f;
+    for (int j = lo; j < hi; ++j) cb[j] = __fadd_rn(cb[j], add);
+    // cb[j] now sums the terms of positions j..m-1, i.e. of rows j+1..m
+    if (lane == 0) cb[m] = 0.0f;
+    __syncwarp();
+}
 
 // One work item on one warp: a tile of nlanes (<= 32) consecutive windows
 // starting at i0, or (list_mode) the single window i0.  STAGE: copy the
@@ -110,7 +152,9 @@ struct TileCtx {
 // JW: 0 = the DP columns' query values held in registers, one window of 32
 // blocks; JW >= 1 = the values streamed from C.zq at every step, JW windows of
 // 32 blocks (fewer registers per thread, more resident warps).
-template <int K, int BAND, bool LB, int JW, bool STAGE = true, int ECM = 1, typename CountF>
+// TIGHT: upper-bound tightening for the survivors (needs C.cbw and the lower
+// bounds; compiled out otherwise).
+template <int K, int BAND, bool LB, int JW, bool STAGE = true, int ECM = 1, bool TIGHT = false, typename CountF>
 __device__ __forceinline__ void process_tile(const TileCtx& C, float* s_r, bool list_mode, int64_t i0,
                                              int nlanes, CountF count) {
     const int lane = threadIdx.x & 31;
@@ -259,9 +303,10 @@ __device__ __forceinline__ void process_tile(const TileCtx& C, float* s_r, bool 
             if (lane == 0) count(kCntRecheck, 1);
             continue;
         }
+        if (TIGHT) tightening_terms(C, s_r + off, a_s, cw_s, isd_s);
         constexpr int kJ = JW > 0 ? JW : dtw_windows(K, BAND);
-        const DtwOut o = dtw_warp<K, BAND, kJ, (JW > 0)>(s_r + off, a_s, cw_s, isd_s, C.zq, m, m, C.w, C.bsf,
-                                                     ub, C.dbg);
+        const DtwOut o = dtw_warp<K, BAND, kJ, (JW > 0), TIGHT>(s_r + off, a_s, cw_s, isd_s, C.zq, m, m, C.w,
+                                                            C.bsf, ub, C.dbg, TIGHT ? C.cbw : nullptr);
         if (lane == 0) {
             count(kCntSteps, static_cast<unsigned long long>(o.steps));
             count(kCntCells, static_cast<unsigned long long>(o.busy) * K);
@@ -307,7 +352,7 @@ __host__ __device__ constexpr int mode_min_blocks(int K, int BAND, int JW) {
 // JW: 0 for the column values in registers; JW >= 1 streams them from the
 // query in shared memory with JW windows of 32 blocks (the widest re-run level
 // uses four: 4096 columns at K = 32, one resident block per SM).
-template <int K, int BAND, bool LB, int JW = 0>
+template <int K, int BAND, bool LB, int JW = 0, bool TIGHT = false>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32, mode_min_blocks(K, BAND, JW))
 search_kernel(const SearchArgs A) {
     extern __shared__ __align__(16) float smem[];
@@ -366,6 +411,7 @@ search_kernel(const SearchArgs A) {
     C.ovf_cap = A.ovf_cap;
     C.tag = 0;
     C.lost = nullptr;
+    C.cbw = A.cb ? A.cb + (static_cast<int64_t>(blockIdx.x) * (blockDim.x >> 5) + warp) * A.cb_stride : nullptr;
     C.dbg = A.dbg;
 
     for (;;) {
@@ -375,10 +421,11 @@ search_kernel(const SearchArgs A) {
         if (item >= nitems) break;
         if (!list_mode) {
             const int64_t i0 = static_cast<int64_t>(item) * 32;
-            process_tile<K, BAND, LB, JW>(C, s_r, false, i0, static_cast<int>(A.nw - i0 < 32 ? A.nw - i0 : 32),
+            process_tile<K, BAND, LB, JW, true, 1, TIGHT>(C, s_r, false, i0,
+                                                          static_cast<int>(A.nw - i0 < 32 ? A.nw - i0 : 32),
                                             count);
         } else {
-            process_tile<K, BAND, LB, JW>(C, s_r, true, A.ovf_in[item] & 0xffffffffll, 1, count);
+            process_tile<K, BAND, LB, JW, true, 1, TIGHT>(C, s_r, true, A.ovf_in[item] & 0xffffffffll, 1, count);
         }
     }
 

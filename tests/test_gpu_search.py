@@ -146,3 +146,23 @@ def test_wide_query_without_seed():
     check_topk(gi, gd, oi, od, Q, R, 1500)
     gi, gd = run(Q, R, 1500, 2, no_seed=True)
     check_topk(gi, gd, oi, od, Q, R, 1500)
+
+
+@pytest.mark.parametrize("m,w,k", [(128, 13, 1), (256, 40, 5), (512, 512, 2), (1500, 300, 1)])
+def test_tightening_changes_work_not_results(m, w, k):
+    """Upper-bound tightening with the LB_Keogh EQ terms: bit-identical results
+    and audit decisions, no more DTW steps than without it."""
+    R = synth.random_walk(120_000, 70 + m)
+    Q = synth.random_walk(m, 71 + m)
+    Rd, Qd = dev(R), dev(Q)
+    i1, d1, c1 = api.subseq_search(Qd, Rd, w, k, return_counters=True, tighten=True)
+    i0, d0, c0 = api.subseq_search(Qd, Rd, w, k, return_counters=True)
+    np.testing.assert_array_equal(d1.cpu().numpy(), d0.cpu().numpy())
+    np.testing.assert_array_equal(i1.cpu().numpy(), i0.cpu().numpy())
+    ub = float(d0.cpu().numpy()[-1])
+    _, a1, e1 = api.subseq_search(Qd, Rd, w, k, audit_ub=ub, return_counters=True, tighten=True)
+    _, a0, e0 = api.subseq_search(Qd, Rd, w, k, audit_ub=ub, return_counters=True)
+    np.testing.assert_array_equal(a1.cpu().numpy(), a0.cpu().numpy())
+    for key in ("kim_pruned", "eq_pruned", "ec_pruned", "dtw_abandoned", "dtw_completed"):
+        assert e1[key] == e0[key], key
+    assert e1["steps"] <= e0["steps"]
