@@ -75,7 +75,9 @@ extern "C" {
 #define EAPDTW_CNT_NS_SEED 13       /* sampled upper-bound seed */
 #define EAPDTW_CNT_NS_TOTAL 14      /* whole call, first to last kernel */
 #define EAPDTW_CNT_LAUNCHES 15      /* kernels launched by the call */
-#define EAPDTW_NCOUNTERS 16
+#define EAPDTW_CNT_PROBE_OVERFLOW 16 /* overflows among the first-level probe's windows (-1: no probe) */
+#define EAPDTW_CNT_FIRST_TILE 17    /* DP cells per lane of the first level after the probe */
+#define EAPDTW_NCOUNTERS 18
 
 /* eapdtw_strerror: static description of a return code (never NULL). */
 const char* eapdtw_strerror(int32_t code);

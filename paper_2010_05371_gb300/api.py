@@ -21,10 +21,11 @@ _lib = None
 _HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include",
                        "eapdtw.h")
 
-NCOUNTERS = 16
+NCOUNTERS = 18
 COUNTER_NAMES = ("windows", "kim_pruned", "eq_pruned", "ec_pruned", "dtw_abandoned",
                  "dtw_completed", "cells", "lb_recheck", "overflow", "steps", "ns_main",
-                 "ns_wider", "ns_prep", "ns_seed", "ns_total", "launches")
+                 "ns_wider", "ns_prep", "ns_seed", "ns_total", "launches", "probe_overflow",
+                 "first_tile")
 
 
 class SearchOpts(C.Structure):

@@ -22,6 +22,13 @@ constexpr int kMaxLevels = 4;
 constexpr int kSeedSamples = 4096;
 constexpr int kSeedBest = 32;
 constexpr float kLbScale = 1.0001f;   // prune iff lb > ub * kLbScale (FP32 rounding margin)
+// First-level probe: kProbeSamples windows spread evenly over the reference run
+// through EAPrunedDTW at the planned K (after the seed pass, under its bound);
+// if more than kProbeRate of them overflow the warp's window, the whole first
+// level runs one level wider (the live regions are too wide for the planned K,
+// and re-running a window costs its partial first run on top of the wider run).
+constexpr int kProbeSamples = 2048;
+constexpr double kProbeRate = 0.05;
 
 // Work levels: the first launch uses K cells per lane; windows whose live
 // region overflows the warp's window of 32 blocks are re-run with 2K, up to 32.
@@ -105,6 +112,7 @@ struct Scratch {
     // upper-bound tightening rows
     float* cb = nullptr;
     int64_t cap_cb = 0;
+    long long* probe_list = nullptr;  // the first-level probe's sampled windows
     // host-pointer entry points
     float *dQ = nullptr, *dR = nullptr;
     int64_t cap_dq = 0, cap_dr = 0;
@@ -127,9 +135,11 @@ enum IntSlot : int {
     kBad = kOvf0 + kMaxLevels + 1,
     kNBest = kBad + 1,
     kSeedOvf = kNBest + 1,
+    kWorkTail = kSeedOvf + 1,     // probe: entries of the sample list; kWorkTail + 1: its work counter
+    kProbeCount = kWorkTail + 2,  // overflows among the probe's windows
     kNumInts = 32
 };
-static_assert(kSeedOvf < kNumInts, "int slots");
+static_assert(kProbeCount < 24, "int slots (24.. hold the device self-check record)");
 
 // (Re)allocate p with room for n elements (previous contents are dropped).
 template <typename T>
@@ -166,7 +176,8 @@ Scratch* scratch_for_current_device(int* dev_out) {
             cudaMallocHost(reinterpret_cast<void**>(&s->host_state), 1024) != cudaSuccess ||
             cudaMalloc(reinterpret_cast<void**>(&s->seed_ed), sizeof(float) * kSeedSamples) != cudaSuccess ||
             cudaMalloc(reinterpret_cast<void**>(&s->seed_idx), sizeof(int) * kSeedSamples) != cudaSuccess ||
-            cudaMalloc(reinterpret_cast<void**>(&s->seed_best), sizeof(long long) * 64) != cudaSuccess) {
+            cudaMalloc(reinterpret_cast<void**>(&s->seed_best), sizeof(long long) * 64) != cudaSuccess ||
+            cudaMalloc(reinterpret_cast<void**>(&s->probe_list), sizeof(long long) * kProbeSamples) != cudaSuccess) {
             cudaGetLastError();
             delete s;
             return nullptr;
@@ -305,6 +316,10 @@ int32_t search_impl(Scratch& S, const float* Q, int64_t lQ, const float* R, int6
         launches += 3;
     }
     CK(cudaEventRecord(S.ev[2], st));
+    const bool probe = !(opts && opts->tile) && plan.nlev >= 2 && !plan.wide[0] && !plan.wide[1] &&
+                       nw >= 256 * static_cast<int64_t>(kProbeSamples);
+    int64_t probe_ovf = -1;
+    int first_tile = plan.K[0];
     for (int lev = 0; lev < plan.nlev; ++lev) {
         SearchArgs la = a;
         la.work_counter = ints + kWork0 + lev;
@@ -319,6 +334,38 @@ int32_t search_impl(Scratch& S, const float* Q, int64_t lQ, const float* R, int6
         const bool lb = use_lb && lev == 0;
         if (plan.wide[lev]) {
             CK(launch_search_wide(plan.band[lev], la, search_blocks_wide(plan.band[lev], m), st));
+        } else if (lev == 0 && probe) {
+            // the probe (sampled windows, single-window mode, overflows only
+            // counted), then the first level at the planned or the next width:
+            // both launches are enqueued, and each reads the probe's count on the
+            // device and exits at once unless it is the chosen one
+            const bool tight = tighten && lb;
+            CK(launch_probe_list(S.probe_list, kProbeSamples, nw, ints + kWorkTail, st));
+            SearchArgs pa = a;
+            pa.use_lb = 0;
+            pa.work_counter = ints + kWorkTail + 1;
+            pa.ovf_in = S.probe_list;
+            pa.ovf_in_count = ints + kWorkTail;
+            pa.ovf_in_cap = kProbeSamples;
+            pa.ovf_out = nullptr;
+            pa.ovf_out_count = ints + kProbeCount;
+            pa.ovf_cap = 0;
+            pa.counters = S.seed_counters();   // kept apart from the search's own counts
+            CK(launch_search(plan.K[0], plan.band[0], false, pa, search_blocks(plan.K[0], plan.band[0], false, m), st));
+            launches += 2;
+            const int threshold = static_cast<int>(kProbeRate * kProbeSamples);
+            for (int L = 0; L < 2; ++L) {
+                SearchArgs lt = la;
+                lt.ovf_out = S.ovf[L & 1];
+                lt.ovf_out_count = ints + kOvf0 + L;
+                lt.gate_count = ints + kProbeCount;
+                lt.gate_threshold = threshold;
+                lt.gate_wider = L;
+                CK(launch_search(plan.K[L], plan.band[L], lb, lt, search_blocks(plan.K[L], plan.band[L], lb, m, tight),
+                                 st, tight));
+                ++launches;
+            }
+            probe_ovf = threshold;   // marks that a probe ran (the count is read back below)
         } else {
             const bool tight = tighten && lb;   // first level only
             CK(launch_search(plan.K[lev], plan.band[lev], lb, la, search_blocks(plan.K[lev], plan.band[lev], lb, m, tight),
@@ -351,6 +398,12 @@ int32_t search_impl(Scratch& S, const float* Q, int64_t lQ, const float* R, int6
         opts->counters[EAPDTW_CNT_NS_SEED] = ns(1, 2);
         opts->counters[EAPDTW_CNT_NS_TOTAL] = ns(0, 5);
         opts->counters[EAPDTW_CNT_LAUNCHES] = launches;
+        if (probe_ovf >= 0) {
+            probe_ovf = hi[kProbeCount];
+            if (probe_ovf > static_cast<int>(kProbeRate * kProbeSamples)) first_tile = plan.K[1];
+        }
+        opts->counters[EAPDTW_CNT_PROBE_OVERFLOW] = probe_ovf;
+        opts->counters[EAPDTW_CNT_FIRST_TILE] = first_tile;
     }
 #ifdef EAPDTW_DEVICE_CHECKS
     if (hi[24]) {
@@ -531,9 +584,10 @@ int32_t eapdtw_release_scratch(void) {
         release(S->zq); release(S->uq); release(S->lq); release(S->zqo); release(S->ord);
         release(S->ovf[0]); release(S->ovf[1]); release(S->cb);
         release(S->dQ); release(S->dR); release(S->dIdx); release(S->dDist);
-        release(S->state); release(S->seed_ed); release(S->seed_idx); release(S->seed_best);
+        release(S->state); release(S->seed_ed); release(S->seed_idx); release(S->seed_best); release(S->probe_list);
         if (S->host_state) cudaFreeHost(S->host_state);
         S->host_state = nullptr;
+
     }
     delete S;
     g_scratch[dev] = nullptr;

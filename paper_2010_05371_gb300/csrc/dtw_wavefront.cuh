@@ -58,7 +58,12 @@
 namespace eapdtw {
 
 constexpr unsigned kFull = 0xffffffffu;
-constexpr int kCheckEvery = 8;  // steps between border / abandon checks (power of 2)
+// Steps between border / abandon checks (a power of 2; a compile-time knob for
+// tuning experiments).
+#ifndef EAPDTW_CHECK_EVERY
+#define EAPDTW_CHECK_EVERY 8
+#endif
+constexpr int kCheckEvery = EAPDTW_CHECK_EVERY;
 
 struct DtwOut {
     float dist;     // DTW value or +inf

@@ -25,6 +25,8 @@ cudaError_t launch_seed(const RefView& ref, const float* zq, int m, int64_t nw, 
                         int* nbest_out, cudaStream_t s);
 cudaError_t launch_finalize(const unsigned long long* slots, int k, int64_t* out_idx,
                             double* out_dist, cudaStream_t s);
+// ns window indices spread evenly over [0, nw) into list; *count = ns.
+cudaError_t launch_probe_list(long long* list, int ns, int64_t nw, int* count, cudaStream_t s);
 
 // search_kernel<K, BAND, LB> for K in {4, 8, 16, 32}, BAND in {0, 1, 2} and
 // LB in {false, true}; one translation unit per K.  search_blocks gives the

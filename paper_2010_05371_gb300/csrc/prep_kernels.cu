@@ -288,6 +288,15 @@ __global__ void env_level_kernel(const float* __restrict__ smax, const float* __
 }
 
 // ---------------------------------------------------------------------------
+// The first-level probe's windows: ns indices spread evenly over [0, nw).
+// ---------------------------------------------------------------------------
+__global__ void probe_list_kernel(long long* list, int ns, int64_t nw, int* count) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s < ns) list[s] = ns > 1 ? (nw - 1) * s / (ns - 1) : 0;
+    if (s == 0) *count = ns;
+}
+
+// ---------------------------------------------------------------------------
 // Search state initialisation.
 // ---------------------------------------------------------------------------
 __global__ void init_state_kernel(unsigned long long* slots, int k, float* ub_seed,
@@ -586,6 +595,11 @@ cudaError_t launch_env_level(const float* smax, const float* smin, int64_t n, in
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     env_level_kernel<<<sms * 8, 256, 0, s>>>(smax, smin, n, half, dmax, dmin);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_probe_list(long long* list, int ns, int64_t nw, int* count, cudaStream_t s) {
+    probe_list_kernel<<<(ns + 255) / 256, 256, 0, s>>>(list, ns, nw, count);
     return cudaGetLastError();
 }
 

@@ -7,28 +7,60 @@
 namespace eapdtw {
 
 namespace {
+// Per device: the shared-memory size the kernel is currently allowed, and the
+// resident blocks for the last query length asked (host-side caches, so that a
+// launch does not repeat the attribute and occupancy calls).
+template <int BAND, bool LB, bool TIGHT>
+struct LaunchCache {
+    static int smem_allowed[64];
+    static int last_m[64];
+    static int last_blocks[64];
+};
+template <int BAND, bool LB, bool TIGHT> int LaunchCache<BAND, LB, TIGHT>::smem_allowed[64] = {};
+template <int BAND, bool LB, bool TIGHT> int LaunchCache<BAND, LB, TIGHT>::last_m[64] = {};
+template <int BAND, bool LB, bool TIGHT> int LaunchCache<BAND, LB, TIGHT>::last_blocks[64] = {};
+
+inline int current_device() {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    return dev & 63;
+}
+
+template <int BAND, bool LB, bool TIGHT>
+cudaError_t allow_smem(size_t sm, int dev) {
+    using C = LaunchCache<BAND, LB, TIGHT>;
+    if (static_cast<int>(sm) <= C::smem_allowed[dev]) return cudaSuccess;
+    const cudaError_t e = cudaFuncSetAttribute(search_kernel<4, BAND, LB, 0, TIGHT>,
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(sm));
+    if (e == cudaSuccess) C::smem_allowed[dev] = static_cast<int>(sm);
+    return e;
+}
+
 template <int BAND, bool LB, bool TIGHT>
 cudaError_t launch_band(const SearchArgs& args, int blocks, cudaStream_t s) {
     const size_t sm = search_smem_bytes(args.q.m);
-    cudaError_t e = cudaFuncSetAttribute(search_kernel<4, BAND, LB, 0, TIGHT>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(sm));
+    const cudaError_t e = allow_smem<BAND, LB, TIGHT>(sm, current_device());
     if (e != cudaSuccess) return e;
     search_kernel<4, BAND, LB, 0, TIGHT><<<blocks, search_warps(args.q.m) * 32, sm, s>>>(args);
     return cudaGetLastError();
 }
 template <int BAND, bool LB, bool TIGHT>
 int occupancy_blocks(int m) {
+    using C = LaunchCache<BAND, LB, TIGHT>;
+    const int dev = current_device();
+    if (C::last_m[dev] == m && C::last_blocks[dev] > 0) return C::last_blocks[dev];
     const size_t sm = search_smem_bytes(m);
-    cudaFuncSetAttribute(search_kernel<4, BAND, LB, 0, TIGHT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         static_cast<int>(sm));
+    allow_smem<BAND, LB, TIGHT>(sm, dev);
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, search_kernel<4, BAND, LB, 0, TIGHT>,
                                                       search_warps(m) * 32, sm) != cudaSuccess)
         per_sm = 1;
-    int dev = 0, sms = 0;
-    cudaGetDevice(&dev);
+    int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    return (per_sm > 0 ? per_sm : 1) * sms;
+    const int blocks = (per_sm > 0 ? per_sm : 1) * sms;
+    C::last_m[dev] = m;
+    C::last_blocks[dev] = blocks;
+    return blocks;
 }
 template <bool LB, bool TIGHT>
 cudaError_t launch_lb(int band, const SearchArgs& args, int blocks, cudaStream_t s) {

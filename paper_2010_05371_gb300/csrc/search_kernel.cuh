@@ -46,6 +46,12 @@ struct SearchArgs {
     int ovf_in_cap;           // entries beyond the capacity were dropped by the producer
     float* cb;                // upper-bound tightening scratch: cb_stride floats per warp of the grid, or nullptr
     int cb_stride;
+    int64_t tile_lo, tile_hi; // tile mode: tiles [tile_lo, tile_hi) of 32 windows (tile_hi 0: all)
+    // Gate (or nullptr): the launch runs only if (*gate_count > gate_threshold) == gate_wider,
+    // a decision every block reads from device memory written by an earlier launch.
+    const int* gate_count;
+    int gate_threshold;
+    int gate_wider;
     int* dbg;                 // device self-check record (EAPDTW_DEVICE_CHECKS builds only)
 };
 
@@ -356,6 +362,7 @@ template <int K, int BAND, bool LB, int JW = 0, bool TIGHT = false>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32, mode_min_blocks(K, BAND, JW))
 search_kernel(const SearchArgs A) {
     extern __shared__ __align__(16) float smem[];
+    if (A.gate_count && ((*A.gate_count > A.gate_threshold) ? 1 : 0) != A.gate_wider) return;  // uniform
     const int m = A.q.m;
     const int mp = query_pad(m);
     float* s_zq = smem;
@@ -380,7 +387,9 @@ search_kernel(const SearchArgs A) {
     __syncthreads();
 
     const bool list_mode = A.ovf_in != nullptr;
-    int64_t nitems = (A.nw + 31) / 32;
+    const int64_t tile_lo = A.tile_lo;
+    const int64_t tile_hi = A.tile_hi > 0 ? A.tile_hi : (A.nw + 31) / 32;
+    int64_t nitems = tile_hi - tile_lo;
     if (list_mode) {
         const int c = *A.ovf_in_count;
         nitems = c < A.ovf_in_cap ? c : A.ovf_in_cap;
@@ -420,7 +429,7 @@ search_kernel(const SearchArgs A) {
         item = __shfl_sync(kFull, item, 0);
         if (item >= nitems) break;
         if (!list_mode) {
-            const int64_t i0 = static_cast<int64_t>(item) * 32;
+            const int64_t i0 = (tile_lo + item) * 32;
             process_tile<K, BAND, LB, JW, true, 1, TIGHT>(C, s_r, false, i0,
                                                           static_cast<int>(A.nw - i0 < 32 ? A.nw - i0 : 32),
                                             count);
