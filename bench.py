@@ -49,9 +49,10 @@ GOLDEN = os.path.join(ROOT, "tests", "golden", "bench_large_oracle.json")
 # fma(d, d, .) -- four FP32-pipe instructions.
 OPS_PER_CELL = 4
 FP32_LANES_PER_SM = 128
-# DRAM bytes (read + write) of the search kernel per search, from ncu; None until
-# captured for the current kernel (see profiles/).
-TRAFFIC_BYTES_PER_SEARCH = None
+# DRAM bytes (read + write) of the dominant search kernel per search: the ncu
+# capture of the K = 16 first-level launch at n = 1e7 (208.9 MB), scaled to the
+# workload's 2e7 windows (profiles/search_kernel_nolb_k16_1e7.md).
+TRAFFIC_BYTES_PER_SEARCH = 4.18e8
 # CPU baseline sample (oracle): windows of the cascade (w=103) and nolb (w=1024) searches
 CPU_SAMPLE = {"cascade_windows": 2_000_000, "nolb_windows": 200_000, "query_seed": 1}
 
@@ -339,13 +340,16 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--mode", default="all", choices=["all", "cascade", "nolb"],
                     help="searches per step (profiling aid; the benchmark is 'all')")
+    ap.add_argument("--queries", default="1,2,3,4",
+                    help="query seeds of the step (profiling aid; the benchmark is all four)")
     ap.add_argument("--batch-queries", type=int, default=16,
                     help="queries of the batched sample (each against 8 references); 0 skips it")
     ap.add_argument("--serve-requests", type=int, default=24, help="requests per serving run; 0 skips it")
     ap.add_argument("--serve-active", type=int, default=16, help="state slots of the serving loop")
     ap.add_argument("--serve-n", type=int, default=SERVE_N, help="serving reference length")
     args = ap.parse_args()
-    global SEARCHES
+    global SEARCHES, QUERY_SEEDS
+    QUERY_SEEDS = tuple(int(x) for x in args.queries.split(","))
     if args.mode == "cascade":
         SEARCHES = [SEARCHES[0]]
     elif args.mode == "nolb":
