@@ -136,6 +136,9 @@ int32_t eap_dtw_host(const float* S, int64_t lS, const float* T, int64_t lT, int
 int32_t subseq_search(const float* Q, int64_t lQ, const float* R, int64_t lR, int64_t w,
                       int32_t k, int64_t* out_idx, double* out_dist, void* stream);
 
+#define EAPDTW_COST_SQUARED 0
+#define EAPDTW_COST_ABSOLUTE 1
+
 /* Options of subseq_search_ex (zero-initialise, then set fields). */
 typedef struct {
     int32_t no_lb;        /* 1: skip LB_Kim / LB_Keogh ("nolb" variant of Section 5) */
@@ -150,7 +153,12 @@ typedef struct {
                              ub.  Changes the work done, never the result.  First level of the
                              search, lower bounds on.  Off by default: it saves DTW steps but
                              costs more time than it saves on the measured workloads. */
-    int32_t reserved[7];
+    int32_t cost;         /* pointwise cost of the DTW recurrence: EAPDTW_COST_SQUARED (0, Eq. 5)
+                             or EAPDTW_COST_ABSOLUTE (1, |a - b|: another elastic distance with
+                             the same recurrence, Section 6).  The absolute cost requires
+                             no_lb = 1 (LB_Kim / LB_Keogh bound the squared cost) and runs
+                             without the sampled seed (it is a squared distance). */
+    int32_t reserved[6];
 } eapdtw_search_opts;
 
 /* subseq_search_ex - subseq_search with options (opts may be NULL). */

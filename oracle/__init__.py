@@ -93,6 +93,12 @@ def _bind(L):
                                      C.c_int, C.c_double, C.c_int, _I64, _D, _I64]
     L.orc_window_stats.restype = None
     L.orc_window_stats.argtypes = [_D, C.c_int64, C.c_int64, _D, _D]
+    if hasattr(L, "orc_dtw_cost"):
+        L.orc_dtw_cost.restype = C.c_double
+        L.orc_dtw_cost.argtypes = [_D, C.c_int64, _D, C.c_int64, C.c_int64, C.c_int]
+        L.orc_search_brute_cost.restype = C.c_int
+        L.orc_search_brute_cost.argtypes = [_D, C.c_int64, _D, C.c_int64, C.c_int64, C.c_int32, C.c_int,
+                                            _I64, _D]
     return L
 
 
@@ -247,6 +253,29 @@ def search_brute(Q, R, w: int, k: int = 1):
 COUNTER_NAMES = ("windows", "kim_pruned", "eq_pruned", "ec_pruned",
                  "dtw_abandoned", "dtw_completed", "cells")
 
+
+
+COST_SQUARED, COST_ABSOLUTE = 0, 1
+
+
+def dtw_cost(S, T, w: int | None = None, cost: int = COST_SQUARED) -> float:
+    """DTW of Eq. 1-4 with the pointwise cost (a-b)^2 (cost 0) or |a-b| (cost 1)."""
+    S, T = _f64(S), _f64(T)
+    if w is None:
+        w = max(len(S), len(T))
+    return float(lib().orc_dtw_cost(_p(S), len(S), _p(T), len(T), int(w), int(cost)))
+
+
+def search_brute_cost(Q, R, w: int, k: int = 1, cost: int = COST_SQUARED):
+    """Brute-force k-NN subsequence search with the given pointwise cost."""
+    Q, R = _f64(Q), _f64(R)
+    idx = np.empty(k, dtype=np.int64)
+    dist = np.empty(k)
+    rc = lib().orc_search_brute_cost(_p(Q), len(Q), _p(R), len(R), int(w), int(k), int(cost),
+                                     idx.ctypes.data_as(_I64), _p(dist))
+    if rc != 0:
+        raise ValueError("search_brute_cost: invalid arguments")
+    return idx, dist
 
 def search_cascade(Q, R, w: int, k: int = 1, use_lb: bool = True, ub_fixed: float = np.nan,
                    nthreads: int = 1):

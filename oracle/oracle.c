@@ -562,3 +562,56 @@ int orc_search_cascade(const double* Q, int64_t m, const double* R, int64_t n, i
 void orc_window_stats(const double* R, int64_t n, int64_t m, double* mu, double* sd) {
     for (int64_t i = 0; i + m <= n; ++i) orc_mean_std(R + i, m, &mu[i], &sd[i]);
 }
+
+/* ------------------------------------------------------------------------ */
+/* Other pointwise costs (Section 6: elastic distances that share DTW's      */
+/* recurrence).  cost_mode 0: (a - b)^2 (Eq. 5); 1: |a - b|.  The recurrence */
+/* of Eq. 1-4 is unchanged: D(i, j) = cost(i, j) + min(D(i-1, j-1),          */
+/* D(i-1, j), D(i, j-1)), D(0, 0) = 0, borders +inf, band |i - j| <= w.      */
+/* ------------------------------------------------------------------------ */
+static inline double cost_of(double a, double b, int cost_mode) {
+    const double d = a - b;
+    return cost_mode == 1 ? fabs(d) : d * d;
+}
+
+/* Full (lS+1) x (lT+1) DTW matrix with the given cost; returns D(lS, lT),  */
+/* NaN on invalid arguments.                                                 */
+double orc_dtw_cost(const double* S, int64_t lS, const double* T, int64_t lT, int64_t w, int cost_mode) {
+    if (bad_args(S, lS, T, lT, w) || (cost_mode != 0 && cost_mode != 1)) return NAN;
+    if (w < abs64(lS - lT)) return ORC_INF;
+    const int64_t W = lT + 1;
+    double* D = (double*)malloc(sizeof(double) * (size_t)((lS + 1) * W));
+    for (int64_t i = 0; i <= lS; ++i)
+        for (int64_t j = 0; j <= lT; ++j) D[i * W + j] = ORC_INF;
+    D[0] = 0.0;
+    for (int64_t i = 1; i <= lS; ++i) {
+        for (int64_t j = 1; j <= lT; ++j) {
+            if (abs64(i - j) > w) continue;
+            D[i * W + j] = cost_of(S[i - 1], T[j - 1], cost_mode) +
+                           min3(D[(i - 1) * W + j - 1], D[(i - 1) * W + j], D[i * W + j - 1]);
+        }
+    }
+    const double out = D[lS * W + lT];
+    free(D);
+    return out;
+}
+
+/* Brute-force subsequence search with the given cost: z-normalise Q and     */
+/* every window R[i..i+m), d_i = orc_dtw_cost(z_i, zQ, w); the k smallest.   */
+int orc_search_brute_cost(const double* Q, int64_t m, const double* R, int64_t n, int64_t w, int32_t k,
+                          int cost_mode, int64_t* idx, double* dist) {
+    if (!Q || !R || !idx || !dist || m <= 0 || n < m || w < 0 || k < 1 || (cost_mode != 0 && cost_mode != 1))
+        return -1;
+    double* zq = (double*)malloc(sizeof(double) * (size_t)m);
+    double* zc = (double*)malloc(sizeof(double) * (size_t)m);
+    topk_t t = {k, 0, (double*)malloc(sizeof(double) * (size_t)k),
+                (int64_t*)malloc(sizeof(int64_t) * (size_t)k)};
+    orc_znorm(Q, m, zq);
+    for (int64_t i = 0; i + m <= n; ++i) {
+        orc_znorm(R + i, m, zc);
+        topk_insert(&t, orc_dtw_cost(zc, m, zq, m, w, cost_mode), i);
+    }
+    topk_out(&t, idx, dist);
+    free(zq); free(zc); free(t.d); free(t.idx);
+    return 0;
+}

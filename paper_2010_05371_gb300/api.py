@@ -37,7 +37,8 @@ class SearchOpts(C.Structure):
         ("ub_fixed", C.c_double),
         ("counters", C.POINTER(C.c_int64)),
         ("tighten", C.c_int32),
-        ("reserved", C.c_int32 * 7),
+        ("cost", C.c_int32),
+        ("reserved", C.c_int32 * 6),
     ]
 
 
@@ -201,10 +202,14 @@ def eap_dtw_host(S, T, w: int | None = None, ub: float = math.inf) -> float:
     return out.value
 
 
-def _opts(no_lb, tile, no_seed, audit_ub, counters, tighten=False):
+COST_SQUARED, COST_ABSOLUTE = 0, 1
+
+
+def _opts(no_lb, tile, no_seed, audit_ub, counters, tighten=False, cost=0):
     o = SearchOpts()
     o.no_lb = int(bool(no_lb))
     o.tighten = int(bool(tighten))
+    o.cost = int(cost)
     o.tile = int(tile)
     o.no_seed = int(bool(no_seed))
     o.audit = int(audit_ub is not None)
@@ -215,7 +220,7 @@ def _opts(no_lb, tile, no_seed, audit_ub, counters, tighten=False):
 
 def subseq_search(Q, R, w: int, k: int = 1, *, no_lb: bool = False, tile: int = 0,
                   no_seed: bool = False, audit_ub: float | None = None, out=None, stream=None,
-                  return_counters: bool = False, tighten: bool = False):
+                  return_counters: bool = False, tighten: bool = False, cost: int = 0):
     """k nearest z-normalised subsequences of R to Q under DTW_w (Section 5).
 
     Q, R: CUDA float32 tensors.  Returns (idx int64[k], dist float64[k]) CUDA
@@ -228,7 +233,7 @@ def subseq_search(Q, R, w: int, k: int = 1, *, no_lb: bool = False, tile: int = 
     else:
         idx, dist = out
     cnt = np.zeros(NCOUNTERS, dtype=np.int64)
-    o = _opts(no_lb, tile, no_seed, audit_ub, cnt, tighten)
+    o = _opts(no_lb, tile, no_seed, audit_ub, cnt, tighten, cost)
     rc = lib().subseq_search_ex(C.c_void_p(Q.data_ptr()), Q.numel(), C.c_void_p(R.data_ptr()),
                                 R.numel(), int(w), int(k), C.byref(o), C.c_void_p(idx.data_ptr()),
                                 C.c_void_p(dist.data_ptr()), _stream_ptr(stream))

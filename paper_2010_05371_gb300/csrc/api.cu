@@ -211,8 +211,12 @@ int32_t search_impl(Scratch& S, const float* Q, int64_t lQ, const float* R, int6
     const int64_t n = lR;
     const int64_t nw = n - m + 1;
     const int wi = static_cast<int>(w < m ? w : m);   // w >= m - 1 is unconstrained
+    const int cost = opts ? opts->cost : 0;
+    if (cost != kCostSquared && cost != kCostAbsolute) return EAPDTW_ERR_INVALID_ARG;
     const bool use_lb = !(opts && opts->no_lb);
-    const bool seed = !(opts && opts->no_seed) && nw >= 2048;
+    if (cost == kCostAbsolute && use_lb) return EAPDTW_ERR_INVALID_ARG;   // bounds are for the squared cost
+    // the seed is a squared Euclidean distance: an upper bound for the squared cost only
+    const bool seed = !(opts && opts->no_seed) && nw >= 2048 && cost == kCostSquared;
     const bool audit = opts && opts->audit;
     if (audit && std::isnan(opts->ub_fixed)) return EAPDTW_ERR_INVALID_ARG;
     if (search_warps(m) < 1) return EAPDTW_ERR_UNSUPPORTED;
@@ -333,7 +337,7 @@ int32_t search_impl(Scratch& S, const float* Q, int64_t lQ, const float* R, int6
         }
         const bool lb = use_lb && lev == 0;
         if (plan.wide[lev]) {
-            CK(launch_search_wide(plan.band[lev], la, search_blocks_wide(plan.band[lev], m), st));
+            CK(launch_search_wide(plan.band[lev], la, search_blocks_wide(plan.band[lev], m, cost), st, cost));
         } else if (lev == 0 && probe) {
             // the probe (sampled windows, single-window mode, overflows only
             // counted), then the first level at the planned or the next width:
@@ -351,7 +355,8 @@ int32_t search_impl(Scratch& S, const float* Q, int64_t lQ, const float* R, int6
             pa.ovf_out_count = ints + kProbeCount;
             pa.ovf_cap = 0;
             pa.counters = S.seed_counters();   // kept apart from the search's own counts
-            CK(launch_search(plan.K[0], plan.band[0], false, pa, search_blocks(plan.K[0], plan.band[0], false, m), st));
+            CK(launch_search(plan.K[0], plan.band[0], false, pa, search_blocks(plan.K[0], plan.band[0], false, m, false, cost),
+                             st, false, cost));
             launches += 2;
             const int threshold = static_cast<int>(kProbeRate * kProbeSamples);
             for (int L = 0; L < 2; ++L) {
@@ -361,15 +366,15 @@ int32_t search_impl(Scratch& S, const float* Q, int64_t lQ, const float* R, int6
                 lt.gate_count = ints + kProbeCount;
                 lt.gate_threshold = threshold;
                 lt.gate_wider = L;
-                CK(launch_search(plan.K[L], plan.band[L], lb, lt, search_blocks(plan.K[L], plan.band[L], lb, m, tight),
-                                 st, tight));
+                CK(launch_search(plan.K[L], plan.band[L], lb, lt,
+                                 search_blocks(plan.K[L], plan.band[L], lb, m, tight, cost), st, tight, cost));
                 ++launches;
             }
             probe_ovf = threshold;   // marks that a probe ran (the count is read back below)
         } else {
             const bool tight = tighten && lb;   // first level only
-            CK(launch_search(plan.K[lev], plan.band[lev], lb, la, search_blocks(plan.K[lev], plan.band[lev], lb, m, tight),
-                             st, tight));
+            CK(launch_search(plan.K[lev], plan.band[lev], lb, la,
+                             search_blocks(plan.K[lev], plan.band[lev], lb, m, tight, cost), st, tight, cost));
         }
         ++launches;
         if (lev == 0) CK(cudaEventRecord(S.ev[3], st));
@@ -598,30 +603,33 @@ int32_t eapdtw_release_scratch(void) {
 
 namespace eapdtw {
 
-cudaError_t launch_search_k4(int band, bool lb, const SearchArgs& args, int blocks, cudaStream_t s, bool tight);
-cudaError_t launch_search_k8(int band, bool lb, const SearchArgs& args, int blocks, cudaStream_t s, bool tight);
-cudaError_t launch_search_k16(int band, bool lb, const SearchArgs& args, int blocks, cudaStream_t s, bool tight);
-cudaError_t launch_search_k32(int band, bool lb, const SearchArgs& args, int blocks, cudaStream_t s, bool tight);
-int search_blocks_k4(int band, bool lb, int m, bool tight);
-int search_blocks_k8(int band, bool lb, int m, bool tight);
-int search_blocks_k16(int band, bool lb, int m, bool tight);
-int search_blocks_k32(int band, bool lb, int m, bool tight);
+cudaError_t launch_search_k4(int band, bool lb, const SearchArgs& args, int blocks, cudaStream_t s, bool tight, int cost);
+cudaError_t launch_search_k8(int band, bool lb, const SearchArgs& args, int blocks, cudaStream_t s, bool tight, int cost);
+cudaError_t launch_search_k16(int band, bool lb, const SearchArgs& args, int blocks, cudaStream_t s, bool tight,
+                              int cost);
+cudaError_t launch_search_k32(int band, bool lb, const SearchArgs& args, int blocks, cudaStream_t s, bool tight,
+                              int cost);
+int search_blocks_k4(int band, bool lb, int m, bool tight, int cost);
+int search_blocks_k8(int band, bool lb, int m, bool tight, int cost);
+int search_blocks_k16(int band, bool lb, int m, bool tight, int cost);
+int search_blocks_k32(int band, bool lb, int m, bool tight, int cost);
 
-cudaError_t launch_search(int K, int band, bool lb, const SearchArgs& args, int blocks, cudaStream_t s, bool tight) {
+cudaError_t launch_search(int K, int band, bool lb, const SearchArgs& args, int blocks, cudaStream_t s, bool tight,
+                          int cost) {
     switch (K) {
-        case 4: return launch_search_k4(band, lb, args, blocks, s, tight);
-        case 8: return launch_search_k8(band, lb, args, blocks, s, tight);
-        case 16: return launch_search_k16(band, lb, args, blocks, s, tight);
-        default: return launch_search_k32(band, lb, args, blocks, s, tight);
+        case 4: return launch_search_k4(band, lb, args, blocks, s, tight, cost);
+        case 8: return launch_search_k8(band, lb, args, blocks, s, tight, cost);
+        case 16: return launch_search_k16(band, lb, args, blocks, s, tight, cost);
+        default: return launch_search_k32(band, lb, args, blocks, s, tight, cost);
     }
 }
 
-int search_blocks(int K, int band, bool lb, int m, bool tight) {
+int search_blocks(int K, int band, bool lb, int m, bool tight, int cost) {
     switch (K) {
-        case 4: return search_blocks_k4(band, lb, m, tight);
-        case 8: return search_blocks_k8(band, lb, m, tight);
-        case 16: return search_blocks_k16(band, lb, m, tight);
-        default: return search_blocks_k32(band, lb, m, tight);
+        case 4: return search_blocks_k4(band, lb, m, tight, cost);
+        case 8: return search_blocks_k8(band, lb, m, tight, cost);
+        case 16: return search_blocks_k16(band, lb, m, tight, cost);
+        default: return search_blocks_k32(band, lb, m, tight, cost);
     }
 }
 

@@ -58,6 +58,8 @@
 namespace eapdtw {
 
 constexpr unsigned kFull = 0xffffffffu;
+constexpr int kCostSquared = 0;   // cost(a, b) = (a - b)^2
+constexpr int kCostAbsolute = 1;  // cost(a, b) = |a - b|
 // Steps between border / abandon checks (a power of 2; a compile-time knob for
 // tuning experiments).
 #ifndef EAPDTW_CHECK_EVERY
@@ -97,7 +99,11 @@ __device__ __forceinline__ float f_nan() { return __int_as_float(0x7fffffff); }
 // in registers (for the widest windows, whose registers would not fit).
 // All 32 lanes call it with identical arguments.
 // TIGHT: upper-bound tightening with cb (see thr below); compiled out otherwise.
-template <int K, int BAND, int J = 1, bool CS = false, bool TIGHT = false>
+// COST: the pointwise cost of the recurrence: kCostSquared, (a - b)^2 (Eq. 5, the
+// paper's); kCostAbsolute, |a - b| (another elastic distance with the same
+// recurrence, Section 6).  Both are non-negative, so the pruning and abandoning
+// arguments hold unchanged.
+template <int K, int BAND, int J = 1, bool CS = false, bool TIGHT = false, int COST = 0>
 __device__ __forceinline__ DtwOut dtw_warp(const float* __restrict__ rows, float a, float cw,
                                            float isd, const float* __restrict__ cols, int nr,
                                            int nc, int w, const BestSoFar bsf, float ub,
@@ -190,7 +196,8 @@ __device__ __forceinline__ DtwOut dtw_warp(const float* __restrict__ rows, float
         for (int k = 0; k < K; ++k) {
             const float top = prv[j][k];
             const float d = __fsub_rn(z, CS ? qs[CS ? k : 0] : zc[CS ? 0 : j][k]);
-            float v = __fmaf_rn(d, d, fminf(fminf(top, diag), left));
+            const float mn = fminf(fminf(top, diag), left);
+            float v = (COST == kCostAbsolute) ? __fadd_rn(fabsf(d), mn) : __fmaf_rn(d, d, mn);
             if (BAND == 1) v = (k == kf) ? INF : v;
             if (BAND == 2) v = (k == kf || k == kf2) ? INF : v;
             diag = top;

@@ -32,13 +32,14 @@ cudaError_t launch_probe_list(long long* list, int ns, int64_t nw, int* count, c
 // LB in {false, true}; one translation unit per K.  search_blocks gives the
 // persistent grid (resident blocks per SM x SMs).
 // tight: the first-level variant with upper-bound tightening (lb only).
+// cost: kCostSquared, or kCostAbsolute (no lower bounds only).
 cudaError_t launch_search(int K, int band, bool lb, const SearchArgs& args, int blocks, cudaStream_t s,
-                          bool tight = false);
-int search_blocks(int K, int band, bool lb, int m, bool tight = false);
+                          bool tight = false, int cost = 0);
+int search_blocks(int K, int band, bool lb, int m, bool tight = false, int cost = 0);
 // The widest re-run level (K = 32, columns streamed from shared memory; two
 // windows, 2048 columns, for m <= 2048; four windows, 4096 columns, beyond).
-cudaError_t launch_search_wide(int band, const SearchArgs& args, int blocks, cudaStream_t s);
-int search_blocks_wide(int band, int m);
+cudaError_t launch_search_wide(int band, const SearchArgs& args, int blocks, cudaStream_t s, int cost = 0);
+int search_blocks_wide(int band, int m, int cost = 0);
 
 // eap_dtw single pair: one warp; wide selects the four-window level.
 cudaError_t launch_pair(int K, int band, bool wide, const float* rows, int nr, const float* cols, int nc,

@@ -160,7 +160,8 @@ __device__ __forceinline__ void tightening_terms(const TileCtx& C, const float* 
 // 32 blocks (fewer registers per thread, more resident warps).
 // TIGHT: upper-bound tightening for the survivors (needs C.cbw and the lower
 // bounds; compiled out otherwise).
-template <int K, int BAND, bool LB, int JW, bool STAGE = true, int ECM = 1, bool TIGHT = false, typename CountF>
+template <int K, int BAND, bool LB, int JW, bool STAGE = true, int ECM = 1, bool TIGHT = false, int COST = 0,
+          typename CountF>
 __device__ __forceinline__ void process_tile(const TileCtx& C, float* s_r, bool list_mode, int64_t i0,
                                              int nlanes, CountF count) {
     const int lane = threadIdx.x & 31;
@@ -311,8 +312,8 @@ __device__ __forceinline__ void process_tile(const TileCtx& C, float* s_r, bool 
         }
         if (TIGHT) tightening_terms(C, s_r + off, a_s, cw_s, isd_s);
         constexpr int kJ = JW > 0 ? JW : dtw_windows(K, BAND);
-        const DtwOut o = dtw_warp<K, BAND, kJ, (JW > 0), TIGHT>(s_r + off, a_s, cw_s, isd_s, C.zq, m, m, C.w,
-                                                            C.bsf, ub, C.dbg, TIGHT ? C.cbw : nullptr);
+        const DtwOut o = dtw_warp<K, BAND, kJ, (JW > 0), TIGHT, COST>(s_r + off, a_s, cw_s, isd_s, C.zq, m, m,
+                                                                  C.w, C.bsf, ub, C.dbg, TIGHT ? C.cbw : nullptr);
         if (lane == 0) {
             count(kCntSteps, static_cast<unsigned long long>(o.steps));
             count(kCntCells, static_cast<unsigned long long>(o.busy) * K);
@@ -358,7 +359,8 @@ __host__ __device__ constexpr int mode_min_blocks(int K, int BAND, int JW) {
 // JW: 0 for the column values in registers; JW >= 1 streams them from the
 // query in shared memory with JW windows of 32 blocks (the widest re-run level
 // uses four: 4096 columns at K = 32, one resident block per SM).
-template <int K, int BAND, bool LB, int JW = 0, bool TIGHT = false>
+// COST: see dtw_warp (the absolute cost is built for the no-lower-bound search only).
+template <int K, int BAND, bool LB, int JW = 0, bool TIGHT = false, int COST = 0>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32, mode_min_blocks(K, BAND, JW))
 search_kernel(const SearchArgs A) {
     extern __shared__ __align__(16) float smem[];
@@ -430,11 +432,12 @@ search_kernel(const SearchArgs A) {
         if (item >= nitems) break;
         if (!list_mode) {
             const int64_t i0 = (tile_lo + item) * 32;
-            process_tile<K, BAND, LB, JW, true, 1, TIGHT>(C, s_r, false, i0,
+            process_tile<K, BAND, LB, JW, true, 1, TIGHT, COST>(C, s_r, false, i0,
                                                           static_cast<int>(A.nw - i0 < 32 ? A.nw - i0 : 32),
                                             count);
         } else {
-            process_tile<K, BAND, LB, JW, true, 1, TIGHT>(C, s_r, true, A.ovf_in[item] & 0xffffffffll, 1, count);
+            process_tile<K, BAND, LB, JW, true, 1, TIGHT, COST>(C, s_r, true, A.ovf_in[item] & 0xffffffffll, 1,
+                                                                count);
         }
     }
 

@@ -166,3 +166,27 @@ def test_tightening_changes_work_not_results(m, w, k):
     for key in ("kim_pruned", "eq_pruned", "ec_pruned", "dtw_abandoned", "dtw_completed"):
         assert e1[key] == e0[key], key
     assert e1["steps"] <= e0["steps"]
+
+
+@pytest.mark.parametrize("n,m,w,k", [(3000, 32, 4, 1), (4000, 200, 200, 3), (3000, 600, 600, 2),
+                                     (2600, 1300, 1300, 1), (5000, 128, 20, 5)])
+def test_absolute_cost_search_vs_brute_force(n, m, w, k):
+    """Another elastic distance with DTW's recurrence: cost |a - b|, searched
+    without lower bounds, across the re-run levels (m up to 1300 unconstrained)."""
+    R = synth.random_walk(n, 90 + m)
+    Q = synth.random_walk(m, 91 + m)
+    oi, od = O.search_brute_cost(Q, R, w, k, O.COST_ABSOLUTE)
+    gi, gd = run(Q, R, w, k, no_lb=True, cost=api.COST_ABSOLUTE)
+    zq = O.znorm(Q)
+    for j in range(k):
+        assert dist_close(float(gd[j]), float(od[j]), m), (j, gd[j], od[j])
+        if gi[j] != oi[j]:
+            rescored = O.dtw_cost(O.znorm(R[gi[j]:gi[j] + m]), zq, w, O.COST_ABSOLUTE)
+            assert dist_close(rescored, float(od[j]), m)
+
+
+def test_absolute_cost_needs_no_lower_bounds():
+    R, Q = dev(synth.random_walk(2000, 1)), dev(synth.random_walk(50, 2))
+    with pytest.raises(api.EapDtwError) as e:
+        api.subseq_search(Q, R, 5, 1, cost=api.COST_ABSOLUTE)
+    assert e.value.code == -1
