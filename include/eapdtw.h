@@ -292,6 +292,29 @@ int32_t eapdtw_autotune(eapdtw_ctx* ctx, const eapdtw_item* items, int32_t n, in
                         void* stream, int32_t* n_tuned);
 
 /* ------------------------------------------------------------------------
+ * Whole-series DTW without an external upper bound (Section 2.3: PrunedDTW's
+ * setting, where no best-so-far exists).  Series are rows of length len,
+ * contiguous, DEVICE arrays; znorm = 1 z-normalises each series first
+ * (population deviation; a constant series becomes zeros).  Window as in
+ * eap_dtw.  len <= EAPDTW_MAX_QUERY.  Blocking.
+ * ------------------------------------------------------------------------ */
+
+/* eapdtw_pairwise - out[i * nb + j] = DTW_w(A_i, B_j) for all pairs (DEVICE,
+ * na * nb doubles).  Each pair runs EAPrunedDTW under its own diagonal cost
+ * (squared Euclidean distance: the cost of an admissible path, so an upper
+ * bound of the DTW, PrunedDTW's threshold), so the values are exact DTW. */
+int32_t eapdtw_pairwise(const float* A, int64_t na, const float* B, int64_t nb, int64_t len, int64_t w,
+                        int32_t znorm, double* out, void* stream);
+
+/* eapdtw_nn - for each test series, the k nearest training series under DTW_w
+ * (1-NN classification for k = 1): out_idx/out_dist[t * k .. t * k + k)
+ * (DEVICE), ascending by (distance, index), (-1, +inf) when ntrain < k.  Each
+ * pair runs EAPrunedDTW against the test's current k-th best distance, with no
+ * lower bounds.  k <= EAPDTW_MAX_K. */
+int32_t eapdtw_nn(const float* train, int64_t ntrain, const float* test, int64_t ntest, int64_t len, int64_t w,
+                  int32_t k, int32_t znorm, int64_t* out_idx, double* out_dist, void* stream);
+
+/* ------------------------------------------------------------------------
  * Serving loop (continuous batching).
  *
  * Not in the paper: a server thread of the context takes requests from any

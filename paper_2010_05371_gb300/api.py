@@ -122,6 +122,10 @@ def lib():
         L.eapdtw_autotune.restype = i32
         L.eapdtw_autotune.argtypes = [vp, C.POINTER(Item), i32, i64, vp, pi32]
         pi64 = C.POINTER(i64)
+        L.eapdtw_pairwise.restype = i32
+        L.eapdtw_pairwise.argtypes = [vp, i64, vp, i64, i64, i64, i32, vp, vp]
+        L.eapdtw_nn.restype = i32
+        L.eapdtw_nn.argtypes = [vp, i64, vp, i64, i64, i64, i32, i32, vp, vp, vp]
         L.eapdtw_serve_start.restype = i32
         L.eapdtw_serve_start.argtypes = [vp, i32, i64]
         L.eapdtw_serve_stop.restype = i32
@@ -271,6 +275,47 @@ def subseq_search_noalloc(Q, R, w: int, idx, dist, stream=None):
                                      R.numel(), int(w), int(k), C.c_void_p(idx.data_ptr()),
                                      C.c_void_p(dist.data_ptr()), _stream_ptr(stream))
     _check(rc, "subseq_search_noalloc")
+    return idx, dist
+
+
+def _series_2d(X, name):
+    import torch
+    X = _dev_f32(X, name)
+    if X.dim() != 2:
+        raise TypeError(f"{name} must be a 2-D tensor (series x points)")
+    return X
+
+
+def pairwise(A, B, w: int | None = None, *, znorm: bool = True, stream=None):
+    """DTW_w of every pair of rows (A_i, B_j) as a (len(A), len(B)) float64 CUDA
+    tensor; each pair pruned under its own diagonal cost (no external bound)."""
+    import torch
+    A, B = _series_2d(A, "A"), _series_2d(B, "B")
+    if A.shape[1] != B.shape[1]:
+        raise ValueError("A and B rows must have the same length")
+    L = A.shape[1]
+    out = torch.empty((A.shape[0], B.shape[0]), dtype=torch.float64, device=A.device)
+    rc = lib().eapdtw_pairwise(C.c_void_p(A.data_ptr()), A.shape[0], C.c_void_p(B.data_ptr()), B.shape[0], L,
+                               int(L if w is None else w), int(bool(znorm)), C.c_void_p(out.data_ptr()),
+                               _stream_ptr(stream))
+    _check(rc, "eapdtw_pairwise")
+    return out
+
+
+def nearest_series(train, test, w: int | None = None, k: int = 1, *, znorm: bool = True, stream=None):
+    """The k nearest rows of train (by DTW_w) of every row of test: (idx, dist)
+    CUDA tensors of shape (len(test), k); 1-NN classification for k = 1."""
+    import torch
+    train, test = _series_2d(train, "train"), _series_2d(test, "test")
+    if train.shape[1] != test.shape[1]:
+        raise ValueError("train and test rows must have the same length")
+    L = train.shape[1]
+    idx = torch.empty((test.shape[0], k), dtype=torch.int64, device=test.device)
+    dist = torch.empty((test.shape[0], k), dtype=torch.float64, device=test.device)
+    rc = lib().eapdtw_nn(C.c_void_p(train.data_ptr()), train.shape[0], C.c_void_p(test.data_ptr()), test.shape[0],
+                         L, int(L if w is None else w), int(k), int(bool(znorm)), C.c_void_p(idx.data_ptr()),
+                         C.c_void_p(dist.data_ptr()), _stream_ptr(stream))
+    _check(rc, "eapdtw_nn")
     return idx, dist
 
 

@@ -79,3 +79,9 @@ def test_serving_argument_errors_need_no_gpu(libpath):
     assert L.eapdtw_serve_stats(None, None, 1) == -1
     assert api.strerror(-9) == "request cancelled"
     assert api.strerror(1) == "pending"
+
+
+def test_whole_series_argument_errors_need_no_gpu(libpath):
+    L = api.lib()
+    assert L.eapdtw_pairwise(None, 1, None, 1, 10, 1, 1, None, None) == -1
+    assert L.eapdtw_nn(None, 1, None, 1, 10, 1, 1, 1, None, None, None) == -1
