@@ -18,7 +18,9 @@ the one-query-per-call path on the same sample of the batched mix (queries of
 uneven lengths and windows, each against 8 references); `serving` runs the
 serving loop (continuous batching) against a resident 1e8-point reference,
 first with every request submitted at once, then with Poisson arrivals at half
-that throughput, and reports p50/p99 latency and queries/s.
+that throughput, and reports p50/p99 latency and queries/s.  `extensions`
+measures the absolute-cost search, upper-bound tightening on and off, the
+pairwise DTW matrix and 1-NN classification.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
 """
@@ -306,6 +308,57 @@ def serving_section(args, dev):
     }
 
 
+def extensions_section(args, dev, R, Qs):
+    """The method's extensions, each measured once after a warm-up (CUDA events
+    inside the library for the searches, host clock around the blocking calls
+    for the whole-series forms)."""
+    import torch
+    from paper_2010_05371_gb300 import api, synth
+    out = {}
+    q = Qs[0]
+    nw = R.numel() - q.numel() + 1
+    # another elastic cost with DTW's recurrence: |a - b|, no lower bounds
+    api.subseq_search(q, R, 1024, 1, no_lb=True, cost=api.COST_ABSOLUTE)
+    _, _, c = api.subseq_search(q, R, 1024, 1, no_lb=True, cost=api.COST_ABSOLUTE, return_counters=True)
+    out["absolute_cost_search"] = {"config": f"query seed {QUERY_SEEDS[0]}, m={q.numel()}, w=1024, no lower bounds, "
+                                             f"cost |a-b|, n={R.numel()}",
+                                   "ms": c["ns_total"] / 1e6, "windows_per_s": nw / (c["ns_total"] / 1e9)}
+    # upper-bound tightening with the LB_Keogh EQ terms, on and off
+    ms = {}
+    for tight in (False, True):
+        api.subseq_search(q, R, 103, 1, tighten=tight)
+        _, _, c = api.subseq_search(q, R, 103, 1, tighten=tight, return_counters=True)
+        ms[tight] = (c["ns_total"] / 1e6, c["steps"])
+    out["tightening"] = {"config": f"query seed {QUERY_SEEDS[0]}, m={q.numel()}, w=103, cascade, n={R.numel()}",
+                         "ms_off": ms[False][0], "ms_on": ms[True][0], "dtw_steps_off": ms[False][1],
+                         "dtw_steps_on": ms[True][1]}
+    # whole series without an external bound
+    L, na = 256, 512
+    A = torch.from_numpy(np.stack([synth.random_walk(L, 5000 + s) for s in range(na)]).astype(np.float32)).to(dev)
+    api.pairwise(A[:64], A[:64], 26)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    api.pairwise(A, A, 26)
+    torch.cuda.synchronize()
+    tp = time.perf_counter() - t0
+    band = L * (2 * 26 + 1) - 26 * 27
+    out["pairwise"] = {"config": f"{na} x {na} random walks of {L} points, z-normalised, w=26",
+                       "s": round(tp, 4), "pairs_per_s": na * na / tp, "band_cells_per_s": na * na * band / tp}
+    ntr, nte = 4096, 256
+    train = torch.from_numpy(np.stack([synth.random_walk(L, 20000 + s) for s in range(ntr)]).astype(np.float32)).to(dev)
+    test = torch.from_numpy(np.stack([synth.random_walk(L, 90000 + s) for s in range(nte)]).astype(np.float32)).to(dev)
+    api.nearest_series(train[:256], test[:16], 26, 1)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    api.nearest_series(train, test, 26, 1)
+    torch.cuda.synchronize()
+    tn = time.perf_counter() - t0
+    out["nn1_classification"] = {"config": f"{nte} test x {ntr} training random walks of {L} points, w=26, k=1",
+                                 "s": round(tn, 4), "test_series_per_s": nte / tn,
+                                 "pairs_per_s": nte * ntr / tn}
+    return out
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -347,6 +400,7 @@ def main():
     ap.add_argument("--serve-requests", type=int, default=24, help="requests per serving run; 0 skips it")
     ap.add_argument("--serve-active", type=int, default=16, help="state slots of the serving loop")
     ap.add_argument("--serve-n", type=int, default=SERVE_N, help="serving reference length")
+    ap.add_argument("--no-extensions", action="store_true", help="skip the extensions object")
     args = ap.parse_args()
     global SEARCHES, QUERY_SEEDS
     QUERY_SEEDS = tuple(int(x) for x in args.queries.split(","))
@@ -504,7 +558,9 @@ def main():
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline()
-    batched = serving = None
+    batched = serving = extensions = None
+    if rank == 0 and world == 1 and not args.no_extensions:
+        extensions = extensions_section(args, dev, R, Qs)
     if rank == 0 and world == 1:
         del R2, Q2, flush
         torch.cuda.empty_cache()
@@ -539,6 +595,7 @@ def main():
             "parity": parity,
             "batched": batched,
             "serving": serving,
+            "extensions": extensions,
             "wall_s": round(t_wall, 3),
         }
         print(json.dumps(line), flush=True)
