@@ -156,8 +156,8 @@ typedef struct {
     int32_t cost;         /* pointwise cost of the DTW recurrence: EAPDTW_COST_SQUARED (0, Eq. 5)
                              or EAPDTW_COST_ABSOLUTE (1, |a - b|: another elastic distance with
                              the same recurrence, Section 6).  The absolute cost requires
-                             no_lb = 1 (LB_Kim / LB_Keogh bound the squared cost) and runs
-                             without the sampled seed (it is a squared distance). */
+                             no_lb = 1 (LB_Kim / LB_Keogh bound the squared cost); its sampled
+                             seed sums |z - q| along the diagonal. */
     int32_t reserved[6];
 } eapdtw_search_opts;
 

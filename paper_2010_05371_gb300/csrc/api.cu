@@ -215,8 +215,7 @@ int32_t search_impl(Scratch& S, const float* Q, int64_t lQ, const float* R, int6
     if (cost != kCostSquared && cost != kCostAbsolute) return EAPDTW_ERR_INVALID_ARG;
     const bool use_lb = !(opts && opts->no_lb);
     if (cost == kCostAbsolute && use_lb) return EAPDTW_ERR_INVALID_ARG;   // bounds are for the squared cost
-    // the seed is a squared Euclidean distance: an upper bound for the squared cost only
-    const bool seed = !(opts && opts->no_seed) && nw >= 2048 && cost == kCostSquared;
+    const bool seed = !(opts && opts->no_seed) && nw >= 2048;
     const bool audit = opts && opts->audit;
     if (audit && std::isnan(opts->ub_fixed)) return EAPDTW_ERR_INVALID_ARG;
     if (search_warps(m) < 1) return EAPDTW_ERR_UNSUPPORTED;
@@ -299,7 +298,7 @@ int32_t search_impl(Scratch& S, const float* Q, int64_t lQ, const float* R, int6
     if (seed && !audit) {
         const int ns = static_cast<int>(nw < kSeedSamples ? nw : kSeedSamples);
         CK(launch_seed(a.ref, S.zq, m, nw, ns, S.seed_ed, S.seed_idx, k, S.ub_seed(), S.seed_best,
-                       kSeedBest, ints + kNBest, st));
+                       kSeedBest, ints + kNBest, st, cost));
         SearchArgs sa = a;
         sa.use_lb = 0;
         sa.work_counter = ints + kWorkSeed;
@@ -313,9 +312,9 @@ int32_t search_impl(Scratch& S, const float* Q, int64_t lQ, const float* R, int6
         const int K = plan.K[plan.nlev - 1];
         const int bd = plan.band[plan.nlev - 1];
         if (plan.wide[plan.nlev - 1]) {
-            CK(launch_search_wide(bd, sa, search_blocks_wide(bd, m) / 4 + 1, st));
+            CK(launch_search_wide(bd, sa, search_blocks_wide(bd, m, cost) / 4 + 1, st, cost));
         } else {
-            CK(launch_search(K, bd, false, sa, search_blocks(K, bd, false, m) / 4 + 1, st));
+            CK(launch_search(K, bd, false, sa, search_blocks(K, bd, false, m, false, cost) / 4 + 1, st, false, cost));
         }
         launches += 3;
     }

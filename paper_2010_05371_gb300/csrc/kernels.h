@@ -22,7 +22,7 @@ cudaError_t launch_init_state(unsigned long long* slots, int k, float* ub_seed,
                               unsigned long long* counters, int* ints, int nints, cudaStream_t s);
 cudaError_t launch_seed(const RefView& ref, const float* zq, int m, int64_t nw, int nsamples,
                         float* ed, int* idx, int k, float* ub_seed, long long* best, int nbest,
-                        int* nbest_out, cudaStream_t s);
+                        int* nbest_out, cudaStream_t s, int cost = 0);
 cudaError_t launch_finalize(const unsigned long long* slots, int k, int64_t* out_idx,
                             double* out_dist, cudaStream_t s);
 // ns window indices spread evenly over [0, nw) into list; *count = ns.

@@ -315,8 +315,10 @@ __global__ void init_state_kernel(unsigned long long* slots, int k, float* ub_se
 // candidates that the search will also visit).
 // ---------------------------------------------------------------------------
 // Sample gw of nsamples (spread evenly over the nw windows) on one warp.
+// cost: kCostSquared sums (z - q)^2; kCostAbsolute sums |z - q| (the diagonal
+// path's cost under the absolute cost, so the same argument bounds it).
 __device__ __forceinline__ void seed_ed_sample(const RefView& ref, const float* __restrict__ zq, int m,
-                                              int64_t nw, int nsamples, int gw, float* ed, int* idx) {
+                                              int64_t nw, int nsamples, int gw, float* ed, int* idx, int cost = 0) {
     const int lane = threadIdx.x & 31;
     const int64_t i = nsamples > 1 ? (nw - 1) * gw / (nsamples - 1) : 0;
     const float* x = ref.R + i;
@@ -331,7 +333,7 @@ __device__ __forceinline__ void seed_ed_sample(const RefView& ref, const float* 
     float s = 0.0f;
     for (int j = lane; j < m; j += 32) {
         const float d = __fsub_rn(znorm1(x[j], a, cw, isd), zq[j]);
-        s = __fmaf_rn(d, d, s);
+        s = (cost == kCostAbsolute) ? __fadd_rn(s, fabsf(d)) : __fmaf_rn(d, d, s);
     }
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     if (lane == 0) {
@@ -342,10 +344,10 @@ __device__ __forceinline__ void seed_ed_sample(const RefView& ref, const float* 
 }
 
 __global__ void seed_ed_kernel(const RefView ref, const float* __restrict__ zq, int m, int64_t nw,
-                               int nsamples, float* ed, int* idx) {
+                               int nsamples, float* ed, int* idx, int cost) {
     const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (gw >= nsamples) return;
-    seed_ed_sample(ref, zq, m, nw, nsamples, gw, ed, idx);
+    seed_ed_sample(ref, zq, m, nw, nsamples, gw, ed, idx, cost);
 }
 
 // One block: ub_seed = the k-th smallest sampled ED (distinct windows; +inf if
@@ -553,10 +555,10 @@ cudaError_t launch_init_state(unsigned long long* slots, int k, float* ub_seed,
 
 cudaError_t launch_seed(const RefView& ref, const float* zq, int m, int64_t nw, int nsamples,
                         float* ed, int* idx, int k, float* ub_seed, long long* best, int nbest,
-                        int* nbest_out, cudaStream_t s) {
+                        int* nbest_out, cudaStream_t s, int cost) {
     const int threads = 256;
     const int blocks = (nsamples * 32 + threads - 1) / threads;
-    seed_ed_kernel<<<blocks, threads, 0, s>>>(ref, zq, m, nw, nsamples, ed, idx);
+    seed_ed_kernel<<<blocks, threads, 0, s>>>(ref, zq, m, nw, nsamples, ed, idx, cost);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     seed_select_kernel<<<1, 1024, 0, s>>>(ed, idx, nsamples, k, ub_seed, best, nbest, nbest_out);
