@@ -190,3 +190,39 @@ def test_absolute_cost_needs_no_lower_bounds():
     with pytest.raises(api.EapDtwError) as e:
         api.subseq_search(Q, R, 5, 1, cost=api.COST_ABSOLUTE)
     assert e.value.code == -1
+
+
+def _golden(name):
+    import json
+    import os
+    with open(os.path.join(os.path.dirname(__file__), "golden", name)) as f:
+        return json.load(f)
+
+
+def _check_nn(gi, gd, nn_index, nn_dist, Q, R, w):
+    m = len(Q)
+    assert dist_close(gd, nn_dist, m), (gd, nn_dist)
+    if gi != nn_index:  # tie-equivalent: the oracle's own distance at the GPU's index
+        rescored = O.dtw(O.znorm(np.asarray(R[gi:gi + m], np.float64)), O.znorm(np.asarray(Q, np.float64)), w)
+        assert dist_close(rescored, nn_dist, m), (gi, rescored, nn_index, nn_dist)
+
+
+def test_large_configs_at_full_size():
+    """The large random-walk and ECG-like configurations at full size (2e7
+    points), against the FP64 oracle's nearest neighbours written by
+    oracle/bench_reference.py and oracle/ecg_reference.py."""
+    g = _golden("bench_large_oracle.json")
+    R = np.asarray(synth.random_walk(20_000_000, 0), np.float32)
+    Rd = dev(R)
+    for e in g["searches"]:
+        Q = synth.random_walk(e["m"], e["query_seed"])
+        gi, gd = api.subseq_search(dev(Q), Rd, e["w"], 1, no_lb=not e["lower_bounds"])
+        _check_nn(int(gi.cpu()[0]), float(gd.cpu()[0]), e["nn_index"], e["nn_dist"], Q, R, e["w"])
+    del Rd
+    g = _golden("ecg_large_oracle.json")
+    R = np.asarray(synth.ecg_like(20_000_000, 0), np.float32)
+    Rd = dev(R)
+    for e in g["searches"]:
+        Q = synth.ecg_query(e["m"], e["query_seed"])
+        gi, gd = api.subseq_search(dev(Q), Rd, e["w"], 1)
+        _check_nn(int(gi.cpu()[0]), float(gd.cpu()[0]), e["nn_index"], e["nn_dist"], Q, R, e["w"])
