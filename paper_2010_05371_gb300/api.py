@@ -475,3 +475,36 @@ class Context:
         out = (C.c_int64 * len(SERVE_STAT_NAMES))()
         _check(lib().eapdtw_serve_stats(self._h, out, len(SERVE_STAT_NAMES)), "eapdtw_serve_stats")
         return dict(zip(SERVE_STAT_NAMES, (int(v) for v in out)))
+
+    # ---- autotuner table: persisted per GPU model ---------------------------
+    def tuning_table(self) -> dict:
+        """The first-level tile choices in effect: {(log2_m, ratio_tenths, band): tile}."""
+        out = {}
+        for lg in range(13):
+            for tenth in range(11):
+                for band in (0, 1):
+                    t = self.get_first_tile(lg, tenth, band)
+                    if t:
+                        out[(lg, tenth, band)] = t
+        return out
+
+    def save_tuning(self, path: str):
+        """Write the tuning table to a JSON file, keyed by this device's name."""
+        import json
+        import torch
+        entries = [[lg, tenth, band, tile] for (lg, tenth, band), tile in sorted(self.tuning_table().items())]
+        with open(path, "w") as f:
+            json.dump({"device": torch.cuda.get_device_name(self.device), "entries": entries}, f, indent=1)
+
+    def load_tuning(self, path: str) -> int:
+        """Load a table written by save_tuning on the same GPU model; returns the
+        number of entries set (0 if the file was written on another model)."""
+        import json
+        import torch
+        with open(path) as f:
+            data = json.load(f)
+        if data.get("device") != torch.cuda.get_device_name(self.device):
+            return 0
+        for lg, tenth, band, tile in data.get("entries", []):
+            self.set_first_tile(lg, tenth, band, tile)
+        return len(data.get("entries", []))

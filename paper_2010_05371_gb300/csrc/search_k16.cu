@@ -6,6 +6,12 @@
 
 namespace eapdtw {
 
+// Column values of the K = 16 kernels: 0 in registers, 1 streamed from the
+// query in shared memory (a tuning knob; 0 is the measured choice).
+#ifndef EAPDTW_K16_JW
+#define EAPDTW_K16_JW 0
+#endif
+
 namespace {
 // Per device: the shared-memory size the kernel is currently allowed, and the
 // resident blocks for the last query length asked (host-side caches, so that a
@@ -30,7 +36,7 @@ template <int BAND, bool LB, bool TIGHT, int COST>
 cudaError_t allow_smem(size_t sm, int dev) {
     using C = LaunchCache<BAND, LB, TIGHT, COST>;
     if (static_cast<int>(sm) <= C::smem_allowed[dev]) return cudaSuccess;
-    const cudaError_t e = cudaFuncSetAttribute(search_kernel<16, BAND, LB, 0, TIGHT, COST>,
+    const cudaError_t e = cudaFuncSetAttribute(search_kernel<16, BAND, LB, EAPDTW_K16_JW, TIGHT, COST>,
                                                cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(sm));
     if (e == cudaSuccess) C::smem_allowed[dev] = static_cast<int>(sm);
     return e;
@@ -41,7 +47,7 @@ cudaError_t launch_band(const SearchArgs& args, int blocks, cudaStream_t s) {
     const size_t sm = search_smem_bytes(args.q.m);
     const cudaError_t e = allow_smem<BAND, LB, TIGHT, COST>(sm, current_device());
     if (e != cudaSuccess) return e;
-    search_kernel<16, BAND, LB, 0, TIGHT, COST><<<blocks, search_warps(args.q.m) * 32, sm, s>>>(args);
+    search_kernel<16, BAND, LB, EAPDTW_K16_JW, TIGHT, COST><<<blocks, search_warps(args.q.m) * 32, sm, s>>>(args);
     return cudaGetLastError();
 }
 template <int BAND, bool LB, bool TIGHT, int COST>
@@ -52,7 +58,7 @@ int occupancy_blocks(int m) {
     const size_t sm = search_smem_bytes(m);
     allow_smem<BAND, LB, TIGHT, COST>(sm, dev);
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, search_kernel<16, BAND, LB, 0, TIGHT, COST>,
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, search_kernel<16, BAND, LB, EAPDTW_K16_JW, TIGHT, COST>,
                                                       search_warps(m) * 32, sm) != cudaSuccess)
         per_sm = 1;
     int sms = 0;

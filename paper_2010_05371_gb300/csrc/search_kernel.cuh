@@ -349,8 +349,11 @@ __host__ __device__ constexpr int search_min_blocks(int K, int BAND) {
     return dtw_windows(K, BAND) > 1 ? (K <= 4 ? 3 : 2) : (K <= 8 ? 4 : (K <= 16 ? EAPDTW_MINB16 : 2));
 }
 // Same for the streamed-column variants (JW windows).
+#ifndef EAPDTW_MINB_CS1
+#define EAPDTW_MINB_CS1 3
+#endif
 __host__ __device__ constexpr int mode_min_blocks(int K, int BAND, int JW) {
-    return JW == 0 ? search_min_blocks(K, BAND) : (JW == 1 ? 3 : (JW == 2 ? 2 : 1));
+    return JW == 0 ? search_min_blocks(K, BAND) : (JW == 1 ? EAPDTW_MINB_CS1 : (JW == 2 ? 2 : 1));
 }
 
 

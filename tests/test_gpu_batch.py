@@ -199,3 +199,17 @@ def test_autotune_keeps_results():
         n = ctx.autotune([(Qd[id(t[0])],) + t[1:] for t in items], sample_windows=1 << 15)
         assert n >= 1
         compare_with_plain(ctx, items, {rid: R})
+
+
+def test_tuning_table_round_trip(tmp_path):
+    with api.Context(0) as ctx:
+        ctx.set_first_tile(7, 3, 1, 16)
+        ctx.set_first_tile(10, 10, 0, 8)
+        assert ctx.tuning_table() == {(7, 3, 1): 16, (10, 10, 0): 8}
+        path = str(tmp_path / "tuning.json")
+        ctx.save_tuning(path)
+    with api.Context(0) as ctx2:
+        assert ctx2.load_tuning(path) == 2
+        assert ctx2.tuning_table() == {(7, 3, 1): 16, (10, 10, 0): 8}
+        ctx2.set_first_tile(7, 3, 1, 0)
+        assert ctx2.tuning_table() == {(10, 10, 0): 8}
