@@ -213,3 +213,39 @@ def test_tuning_table_round_trip(tmp_path):
         assert ctx2.tuning_table() == {(7, 3, 1): 16, (10, 10, 0): 8}
         ctx2.set_first_tile(7, 3, 1, 0)
         assert ctx2.tuning_table() == {(10, 10, 0): 8}
+
+
+def test_batched_mix_sample_against_the_oracle():
+    """64 items of the batched mix (1,024 queries x 8 references, drawn among the
+    four shortest references) as one batch, against the FP64 oracle's k nearest
+    windows written by oracle/batched_reference.py."""
+    import json
+    import os
+    from oracle import batched_reference as B
+    path = os.path.join(os.path.dirname(__file__), "golden", "batched_mix_oracle.json")
+    if not os.path.exists(path):
+        pytest.skip("golden file not written")
+    with open(path) as f:
+        gold = json.load(f)["items"]
+    lens, qs = B.mix()
+    refs_np = {}
+    with api.Context(0) as ctx:
+        rid = {}
+        items = []
+        for e in gold:
+            j = e["ref"]
+            if j not in rid:
+                refs_np[j] = np.asarray(synth.random_walk(lens[j], 100 + j), np.float32)
+                rid[j] = ctx.register(dev(refs_np[j]))
+            m, w, ecg, k = qs[e["query"]]
+            assert (m, w, ecg, k) == (e["m"], e["w"], e["ecg"], e["k"])
+            Q = B.query_values(e["query"], m, ecg)
+            items.append((dev(Q), rid[j], w, k))
+        ctx.autotune(items, sample_windows=1 << 15)
+        bi, bd = ctx.search_batch(items, 5)
+        bi, bd = bi.cpu().numpy(), bd.cpu().numpy()
+    for r, e in enumerate(gold):
+        m, k, w = e["m"], e["k"], e["w"]
+        Q = B.query_values(e["query"], m, e["ecg"])
+        R = refs_np[e["ref"]]
+        check_topk(bi[r, :k], bd[r, :k], np.array(e["idx"]), np.array(e["dist"]), Q, R, w)
