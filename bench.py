@@ -47,9 +47,9 @@ QUERY_SEEDS = (1, 2, 3, 4)
 SEARCHES = [(103, False), (1024, True)]  # (w, no lower bounds)
 METRIC = "candidate windows/s"
 GOLDEN = os.path.join(ROOT, "tests", "golden", "bench_large_oracle.json")
-# Issue slots of the minimal DP cell: d = z - q; min(top, diag); min(., left);
-# fma(d, d, .) -- four FP32-pipe instructions.
-OPS_PER_CELL = 4
+# Issue slots of the minimal DP cell: d = z - q; min(top, diag, left) (one
+# three-operand min); fma(d, d, .) -- three FP32-pipe instructions.
+OPS_PER_CELL = 3
 FP32_LANES_PER_SM = 128
 # DRAM bytes (read + write) of the dominant search kernel per search: the ncu
 # capture of the K = 16 first-level launch at n = 1e7 (208.9 MB), scaled to the

@@ -189,6 +189,15 @@ __device__ __forceinline__ void window_coeffs(const RefView& ref, int64_t i, int
 #define EAPDTW_CHECK(dbg, ok, code, value) true
 #endif
 
+// min(a, b, c) in one instruction (the three-operand min.f32 of sm_100 and
+// later).  Like fminf it ignores a NaN operand; the result is exact, so it
+// equals fminf(fminf(a, b), c) for every input of the DTW recurrence.
+__device__ __forceinline__ float fmin3(float a, float b, float c) {
+    float r;
+    asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
+}
+
 __device__ __forceinline__ float znorm1(float x, float a, float cw, float isd) {
     return __fmul_rn(__fsub_rn(__fsub_rn(x, a), cw), isd);
 }

@@ -196,7 +196,7 @@ __device__ __forceinline__ DtwOut dtw_warp(const float* __restrict__ rows, float
         for (int k = 0; k < K; ++k) {
             const float top = prv[j][k];
             const float d = __fsub_rn(z, CS ? qs[CS ? k : 0] : zc[CS ? 0 : j][k]);
-            const float mn = fminf(fminf(top, diag), left);
+            const float mn = fmin3(top, diag, left);
             float v = (COST == kCostAbsolute) ? __fadd_rn(fabsf(d), mn) : __fmaf_rn(d, d, mn);
             if (BAND == 1) v = (k == kf) ? INF : v;
             if (BAND == 2) v = (k == kf || k == kf2) ? INF : v;
@@ -209,9 +209,9 @@ __device__ __forceinline__ DtwOut dtw_warp(const float* __restrict__ rows, float
         omin[j] = fminf(omin[j], lout[j]);
     };
     auto block_min = [&](int j) {
-        float bmin = prv[j][0];
+        float bmin = fminf(prv[j][0], prv[j][K - 1]);
 #pragma unroll
-        for (int k = 1; k < K; ++k) bmin = fminf(bmin, prv[j][k]);
+        for (int k = 1; k + 1 < K - 1; k += 2) bmin = fmin3(bmin, prv[j][k], prv[j][k + 1]);
         return bmin;
     };
     // Death threshold of window j's block at step `step` (its row r = step - block).
