@@ -84,6 +84,20 @@ struct BestSoFar {
         return fminf(u, s);
     }
 
+    // The same reading split in two, so that the loads' latency can pass
+    // under other work: issue() reads the k-th key and the seed without using
+    // them; finish() turns that reading into the bound load() would return.
+    struct Raw {
+        unsigned long long key;
+        float seed;
+    };
+    __device__ __forceinline__ Raw issue() const {
+        if (audit) return Raw{kEmptyKey, ub_fixed};
+        return Raw{ld_relaxed_u64(slots + (k - 1)), ld_relaxed_f32(ub_seed)};
+    }
+    __device__ __forceinline__ static Raw of(float ub) { return Raw{kEmptyKey, ub}; }
+    __device__ __forceinline__ static float finish(Raw r) { return fminf(key_dist(r.key), r.seed); }
+
     // Insert (d, idx): a chain of atomicMin over the sorted slots.  Each slot
     // keeps the smaller of (its value, the carried key) and the larger one is
     // carried on, so slot s ends as the (s+1)-th smallest key ever inserted,

@@ -159,7 +159,9 @@ __device__ __forceinline__ DtwOut dtw_warp(const float* __restrict__ rows, float
     // border, out-of-band cells, retired blocks), so ub is kept finite: with
     // ub = +inf, a +inf cell would otherwise count as alive.
     ub = fminf(ub, 3.402823466e38f);
-    float ub_next = ub;
+    // The bound read at the last check, applied at the next one (its loads
+    // complete meanwhile).
+    BestSoFar::Raw ub_raw = BestSoFar::of(ub);
     const int bm = (nc - 1) / K;       // block of the last column
     const int km = (nc - 1) - bm * K;
     const int t_end = nr + bm;         // step computing cell (nr, nc)
@@ -229,6 +231,7 @@ __device__ __forceinline__ DtwOut dtw_warp(const float* __restrict__ rows, float
     // dead_a holds the dead lanes of the step before.  Returns true when the
     // candidate is finished (abandoned or overflowed).
     auto check = [&](const float* bmin_b, int t) -> bool {
+        const float ub_next = __shfl_sync(kFull, BestSoFar::finish(ub_raw), 0);  // one reading for the whole warp
 #ifdef EAPDTW_DEVICE_CHECKS
         EAPDTW_CHECK(dbg, __shfl_sync(kFull, t, 0) == t, 13, t);
         EAPDTW_CHECK(dbg, __shfl_sync(kFull, B0, 0) == B0, 14, B0);
@@ -287,7 +290,7 @@ __device__ __forceinline__ DtwOut dtw_warp(const float* __restrict__ rows, float
                 --jact;
             }
         }
-        ub_next = __shfl_sync(kFull, bsf.load(), 0);  // one reading for the whole warp
+        ub_raw = bsf.issue();
 #pragma unroll
         for (int j = 0; j < J; ++j) omin[j] = INF;
         if (d > 0) {
