@@ -409,4 +409,51 @@ __device__ __forceinline__ DtwOut dtw_warp(const float* __restrict__ rows, float
     return out;
 }
 
+// EAPrunedDTW's first rows, one candidate per lane (Algorithm 3, abandoning).
+// Most windows are abandoned within a few rows, while their live cells still
+// sit in the top-left corner of the cost matrix.  corner_dead computes rows
+// and columns 1..kCorner of one window with the wavefront's own operations
+// (the same FP32 values) and reports whether some row r of the corner is
+// entirely > ub while column kCorner has been > ub in every row up to r.
+// Then no cell right of the corner is alive in rows 1..r either: row 1 only
+// grows to the right, and a later cell right of the corner has only dead
+// inputs.  So all of row r is > ub, and Algorithm 3 abandons the window.
+// Needs m >= kCorner and every corner cell inside the band (w >= kCorner - 1).
+constexpr int kCorner = 16;
+constexpr int kCornerMinLanes = 8;   // run it only when this many lanes are alive
+
+template <int COST>
+__device__ __forceinline__ bool corner_dead(const float* x, float a, float cw, float isd, const float* zq, float ub) {
+    const float INF = f_inf();
+    float q[kCorner], prv[kCorner];
+#pragma unroll
+    for (int c = 0; c < kCorner; ++c) {
+        q[c] = zq[c];
+        prv[c] = INF;   // row 0
+    }
+    bool edge = true;   // column kCorner > ub in every row so far
+    for (int r = 0; r < kCorner; ++r) {
+        const float z = znorm1(x[r], a, cw, isd);
+        float diag = r == 0 ? 0.0f : INF;   // D(0, 0) = 0; D(r, 0) = +inf
+        float left = INF;
+#pragma unroll
+        for (int c = 0; c < kCorner; ++c) {
+            const float top = prv[c];
+            const float d = __fsub_rn(z, q[c]);
+            const float mn = fmin3(top, diag, left);
+            const float v = (COST == kCostAbsolute) ? __fadd_rn(fabsf(d), mn) : __fmaf_rn(d, d, mn);
+            diag = top;
+            left = v;
+            prv[c] = v;
+        }
+        float rmin = prv[0];
+#pragma unroll
+        for (int c = 1; c + 1 < kCorner; c += 2) rmin = fmin3(rmin, prv[c], prv[c + 1]);
+        rmin = fminf(rmin, prv[kCorner - 1]);
+        edge = edge && !(prv[kCorner - 1] <= ub);
+        if (edge && !(rmin <= ub)) return true;
+    }
+    return false;
+}
+
 }  // namespace eapdtw

@@ -125,8 +125,18 @@ __global__ void __launch_bounds__(kPairWarps * 32) nn_kernel(const float* __rest
         const int64_t t = static_cast<int64_t>(u) % ntest, blk = static_cast<int64_t>(u) / ntest;
         const BestSoFar bsf{slots + t * EAPDTW_MAX_K, no_seed, k, 0, 0.0f};   // no_seed: +inf in global memory
         const float* q = test + t * len;
-        const int64_t j1 = (blk + 1) * 32 < ntrain ? (blk + 1) * 32 : ntrain;
-        for (int64_t j = blk * 32; j < j1; ++j) {
+        const int64_t j0 = blk * 32;
+        const int64_t j1 = j0 + 32 < ntrain ? j0 + 32 : ntrain;
+        // Lane l first checks the corner of training series j0 + l (rows and
+        // columns 1..kCorner) against the test's current k-th best; the warp
+        // then runs the survivors.
+        bool alive = j0 + lane < j1;
+        if (alive && len >= kCorner && w >= kCorner - 1)
+            alive = !corner_dead<kCostSquared>(train + (j0 + lane) * len, 0.0f, 0.0f, 1.0f, q, bsf.load());
+        unsigned mask = __ballot_sync(kFull, alive);
+        while (mask) {
+            const int64_t j = j0 + (__ffs(mask) - 1);
+            mask &= mask - 1;
             const float ub = __shfl_sync(kFull, bsf.load(), 0);   // one reading for the whole warp
             const DtwOut o = dtw_warp<K, 2, J, (J > 1)>(train + j * len, 0.0f, 0.0f, 1.0f, q, len, len, w, bsf, ub);
             if (lane == 0 && o.dist < f_inf() && o.dist <= ub) bsf.insert(o.dist, static_cast<uint32_t>(j));

@@ -20,6 +20,12 @@ CASES = [
     ("walk", 20_000, 200, 200, 2, 3),
     ("ecg", 40_000, 256, 26, 1, 4),
     ("walk", 9_000, 600, 150, 1, 5),
+    # edges of the per-lane corner check (rows and columns 1..16): the shortest
+    # query and the narrowest band it runs with, and a query just too short
+    ("walk", 20_000, 16, 15, 2, 6),
+    ("walk", 20_000, 16, 16, 1, 7),
+    ("walk", 20_000, 15, 15, 1, 8),
+    ("walk", 20_000, 40, 14, 3, 9),
 ]
 AUDIT_KEYS = ("windows", "kim_pruned", "eq_pruned", "ec_pruned", "dtw_abandoned", "dtw_completed")
 
