@@ -267,6 +267,14 @@ __device__ __forceinline__ DtwOut dtw_warp(const float* __restrict__ rows, float
             return true;
         }
         int d = (cond == kFull) ? 31 : (__ffs(~cond) - 1);
+        // One window: retire lazily.  Dead leading blocks stay dead, so the
+        // slide (two shuffles per DP value and a reload of the column values)
+        // waits until an alive cell comes within 9 blocks of the window's end.
+        // An alive block at step s+1 needs an alive input at step s or s-1 one
+        // block to its left at most, so with nothing alive in lanes 23..31 at
+        // steps t-1 and t, nothing alive reaches the last lane before the next
+        // check.
+        if (J == 1 && d > 0 && (~(dead_a[0] & db[0]) & 0xff800000u) == 0) d = 0;
         // Switch the next window on when an alive cell came within 9 blocks
         // of the end of the last active one; off when the last one and the
         // end of the one before are dead.
