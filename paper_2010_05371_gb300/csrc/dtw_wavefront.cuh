@@ -18,7 +18,8 @@
 //    warp's window is dead and its left neighbour is retired, no later row of
 //    it can be alive, so it is retired and the window slides right (the
 //    discard points of Algorithm 3 moving next_start; the band's left edge
-//    retires blocks the same way).
+//    retires blocks the same way).  With one window the slide is lazy: dead
+//    leading blocks stay in place until the live region nears the window's end.
 //  * Right border (pruning_point, Section 4).  Cells right of the last alive
 //    cell only receive dead inputs from above, so they are dead unless the
 //    left chain keeps them alive; no bookkeeping is needed: they are computed
@@ -32,7 +33,8 @@
 //    candidate with wider blocks (larger K).
 //  * Early abandoning (border collision / full discard line).  When every
 //    block of the window is dead at two consecutive steps, every later cell
-//    has dead inputs only: the result is +inf.
+//    has dead inputs only: the result is +inf.  These checks come every 16
+//    steps with one window in the unconstrained case and every 8 otherwise.
 //  * Upper bound tightening (optional, the UCR Suite's use of LB_Keogh that
 //    Section 5 keeps).  Every warping path visits every row, and a row's cells
 //    cost at least that row's LB_Keogh EQ term, so a cell of row r whose value
@@ -66,6 +68,16 @@ constexpr int kCostAbsolute = 1;  // cost(a, b) = |a - b|
 #define EAPDTW_CHECK_EVERY 8
 #endif
 constexpr int kCheckEvery = EAPDTW_CHECK_EVERY;
+// The same for the unconstrained one-window kernels.  There the per-lane
+// corner check always runs first and removes the windows that die within a
+// few rows, so the survivors live long enough that checking half as often
+// pays.  Banded searches (where the corner check may not run, and short
+// queries abound) and the multi-window levels (whose window switch-on margin
+// is sized for 8) keep 8.
+#ifndef EAPDTW_CHECK_EVERY_ONE
+#define EAPDTW_CHECK_EVERY_ONE 16
+#endif
+constexpr int kCheckEveryOne = EAPDTW_CHECK_EVERY_ONE;
 
 struct DtwOut {
     float dist;     // DTW value or +inf
@@ -159,6 +171,7 @@ __device__ __forceinline__ DtwOut dtw_warp(const float* __restrict__ rows, float
     // border, out-of-band cells, retired blocks), so ub is kept finite: with
     // ub = +inf, a +inf cell would otherwise count as alive.
     ub = fminf(ub, 3.402823466e38f);
+    constexpr int kCE = (J == 1 && BAND == 0) ? kCheckEveryOne : kCheckEvery;   // steps between checks
     // The bound read at the last check, applied at the next one (its loads
     // complete meanwhile).
     BestSoFar::Raw ub_raw = BestSoFar::of(ub);
@@ -227,7 +240,7 @@ __device__ __forceinline__ DtwOut dtw_warp(const float* __restrict__ rows, float
         r = r < 0 ? 0 : (r > nr ? nr : r);
         return fminf(ub, __fsub_rn(__fmul_rn(ub, 1.0001f), cb[r]));
     };
-    // Border / abandon checks after step t (t a multiple of kCheckEvery);
+    // Border / abandon checks after step t (t a multiple of kCE);
     // dead_a holds the dead lanes of the step before.  Returns true when the
     // candidate is finished (abandoned or overflowed).
     auto check = [&](const float* bmin_b, int t) -> bool {
@@ -269,12 +282,12 @@ __device__ __forceinline__ DtwOut dtw_warp(const float* __restrict__ rows, float
         int d = (cond == kFull) ? 31 : (__ffs(~cond) - 1);
         // One window: retire lazily.  Dead leading blocks stay dead, so the
         // slide (two shuffles per DP value and a reload of the column values)
-        // waits until an alive cell comes within 9 blocks of the window's end.
-        // An alive block at step s+1 needs an alive input at step s or s-1 one
-        // block to its left at most, so with nothing alive in lanes 23..31 at
-        // steps t-1 and t, nothing alive reaches the last lane before the next
-        // check.
-        if (J == 1 && d > 0 && (~(dead_a[0] & db[0]) & 0xff800000u) == 0) d = 0;
+        // waits until an alive cell comes within kCE + 1 blocks of the
+        // window's end.  An alive block at step s+1 needs an alive input at
+        // step s or s-1 one block to its left at most, so with nothing alive
+        // in lanes 31-kCE..31 at steps t-1 and t, nothing alive reaches the
+        // last lane before the next check.
+        if (J == 1 && d > 0 && (~(dead_a[0] & db[0]) & (kFull << (31 - kCE))) == 0) d = 0;
         // Switch the next window on when an alive cell came within 9 blocks
         // of the end of the last active one; off when the last one and the
         // end of the one before are dead.
@@ -330,13 +343,13 @@ __device__ __forceinline__ DtwOut dtw_warp(const float* __restrict__ rows, float
 
     int t = 0;  // last completed step
     for (;;) {
-        // Fast path: the next kCheckEvery steps keep every active lane's row
+        // Fast path: the next kCE steps keep every active lane's row
         // inside [1, nr] and stop short of the final step: no per-lane tests.
-        if ((t & (kCheckEvery - 1)) == 0 && t + 1 - (B0 + 32 * jact - 1) >= 1 &&
-            t + kCheckEvery - B0 <= nr && t + kCheckEvery < t_end) {
+        if ((t & (kCE - 1)) == 0 && t + 1 - (B0 + 32 * jact - 1) >= 1 &&
+            t + kCE - B0 <= nr && t + kCE < t_end) {
             float bmin_a[J], bmin_b[J];
 #pragma unroll
-            for (int s = 1; s <= kCheckEvery; ++s) {
+            for (int s = 1; s <= kCE; ++s) {
                 float lin[J];
                 left_inputs(lin);
 #pragma unroll
@@ -346,13 +359,13 @@ __device__ __forceinline__ DtwOut dtw_warp(const float* __restrict__ rows, float
                         const int r = t + s - bj;
                         const float x = EAPDTW_CHECK(dbg, r >= 1 && r <= nr, 11, r) ? rows[r - 1] : 0.0f;
                         cells(j, znorm1(x, a, cw, isd), lin[j], r - w - 1 - (bj * K + 1));
-                        if (s == kCheckEvery - 1) bmin_a[j] = block_min(j);
-                        if (s == kCheckEvery) bmin_b[j] = block_min(j);
+                        if (s == kCE - 1) bmin_a[j] = block_min(j);
+                        if (s == kCE) bmin_b[j] = block_min(j);
                     }
                 }
             }
-            busy += kCheckEvery * jact;
-            t += kCheckEvery;
+            busy += kCE * jact;
+            t += kCE;
 #pragma unroll
             for (int j = 0; j < J; ++j)
                 dead_a[j] = (j < jact) ? __ballot_sync(kFull, !(bmin_a[j] <= thr(j, t - 1))) : kFull;
@@ -361,7 +374,7 @@ __device__ __forceinline__ DtwOut dtw_warp(const float* __restrict__ rows, float
         }
         // General step with per-lane range tests (pipeline fill and drain).
         ++t;
-        const int phase = t & (kCheckEvery - 1);
+        const int phase = t & (kCE - 1);
         float lin[J], bmin[J];
         left_inputs(lin);
 #pragma unroll
@@ -374,7 +387,7 @@ __device__ __forceinline__ DtwOut dtw_warp(const float* __restrict__ rows, float
                     const float x = EAPDTW_CHECK(dbg, r - 1 < nr, 12, r) ? rows[r - 1] : 0.0f;
                     cells(j, znorm1(x, a, cw, isd), lin[j], r - w - 1 - (bj * K + 1));
                     ++busy;
-                    if (phase == 0 || phase == kCheckEvery - 1) bmin[j] = block_min(j);
+                    if (phase == 0 || phase == kCE - 1) bmin[j] = block_min(j);
                 } else {
                     if (r < 1) lout[j] = INF;
                     lprev[j] = lin[j];
@@ -401,7 +414,7 @@ __device__ __forceinline__ DtwOut dtw_warp(const float* __restrict__ rows, float
             out.steps = t;
             break;
         }
-        if (phase == kCheckEvery - 1) {
+        if (phase == kCE - 1) {
 #pragma unroll
             for (int j = 0; j < J; ++j)
                 dead_a[j] = (j < jact) ? __ballot_sync(kFull, !(bmin[j] <= thr(j, t))) : kFull;
