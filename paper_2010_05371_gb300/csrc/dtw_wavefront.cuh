@@ -343,10 +343,13 @@ __device__ __forceinline__ DtwOut dtw_warp(const float* __restrict__ rows, float
 
     int t = 0;  // last completed step
     for (;;) {
-        // Fast path: the next kCE steps keep every active lane's row
-        // inside [1, nr] and stop short of the final step: no per-lane tests.
-        if ((t & (kCE - 1)) == 0 && t + 1 - (B0 + 32 * jact - 1) >= 1 &&
-            t + kCE - B0 <= nr && t + kCE < t_end) {
+        // Fast path: the next kCE steps keep every active lane's row at most
+        // nr and stop short of the final step: no per-lane tests.  A lane
+        // whose row is still below 1 (the pipeline filling) computes too: its
+        // own values and its left input (the previous lane's output for the
+        // same row) are all +inf, so its cells stay +inf (NaN past the last
+        // column), exactly the state it would keep by waiting.
+        if ((t & (kCE - 1)) == 0 && t + kCE - B0 <= nr && t + kCE < t_end) {
             float bmin_a[J], bmin_b[J];
 #pragma unroll
             for (int s = 1; s <= kCE; ++s) {
@@ -357,14 +360,22 @@ __device__ __forceinline__ DtwOut dtw_warp(const float* __restrict__ rows, float
                     if (j < jact) {
                         const int bj = B0 + 32 * j + lane;
                         const int r = t + s - bj;
-                        const float x = EAPDTW_CHECK(dbg, r >= 1 && r <= nr, 11, r) ? rows[r - 1] : 0.0f;
+                        const int rr = r < 1 ? 1 : r;   // rows below 1 read row 1 (their cells stay +inf)
+                        const float x = EAPDTW_CHECK(dbg, rr <= nr, 11, r) ? rows[rr - 1] : 0.0f;
                         cells(j, znorm1(x, a, cw, isd), lin[j], r - w - 1 - (bj * K + 1));
                         if (s == kCE - 1) bmin_a[j] = block_min(j);
                         if (s == kCE) bmin_b[j] = block_min(j);
                     }
                 }
             }
-            busy += kCE * jact;
+            // lane-steps whose row was in [1, nr]
+#pragma unroll
+            for (int j = 0; j < J; ++j) {
+                if (j < jact) {
+                    const int started = t + kCE - (B0 + 32 * j + lane);
+                    busy += started < kCE ? (started > 0 ? started : 0) : kCE;
+                }
+            }
             t += kCE;
 #pragma unroll
             for (int j = 0; j < J; ++j)
