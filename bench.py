@@ -52,9 +52,9 @@ GOLDEN = os.path.join(ROOT, "tests", "golden", "bench_large_oracle.json")
 OPS_PER_CELL = 3
 FP32_LANES_PER_SM = 128
 # DRAM bytes (read + write) of the dominant search kernel per search: the ncu
-# capture of the K = 16 first-level launch at n = 1e7 (209.1 MB), scaled to the
+# capture of the K = 16 first-level launch at n = 1e7 (210.0 MB), scaled to the
 # workload's 2e7 windows (profiles/search_kernel_nolb_k16_1e7.md).
-TRAFFIC_BYTES_PER_SEARCH = 4.18e8
+TRAFFIC_BYTES_PER_SEARCH = 4.20e8
 # CPU baseline sample (oracle): windows of the cascade (w=103) and nolb (w=1024) searches
 CPU_SAMPLE = {"cascade_windows": 2_000_000, "nolb_windows": 200_000, "query_seed": 1}
 
