@@ -61,9 +61,13 @@ extern "C" {
 #define EAPDTW_CNT_KIM_PRUNED 1     /* skipped by LB_Kim > ub */
 #define EAPDTW_CNT_EQ_PRUNED 2      /* skipped by LB_Keogh(EQ) > ub */
 #define EAPDTW_CNT_EC_PRUNED 3      /* skipped by LB_Keogh(EC) > ub */
-#define EAPDTW_CNT_DTW_ABANDONED 4  /* EAPrunedDTW returned +inf (DTW > ub) */
+#define EAPDTW_CNT_DTW_ABANDONED 4  /* EAPrunedDTW returned +inf (DTW > ub), whether the
+                                       per-lane check of the first 16 rows or the warp
+                                       wavefront found the dead row */
 #define EAPDTW_CNT_DTW_COMPLETED 5  /* EAPrunedDTW returned a value <= ub */
-#define EAPDTW_CNT_CELLS 6          /* DP cells executed by the kernel (K per busy lane-step) */
+#define EAPDTW_CNT_CELLS 6          /* DP cells executed by the kernel: K per busy lane-step
+                                       of the wavefront, plus 16 x 16 per window given to
+                                       the per-lane first-rows check */
 #define EAPDTW_CNT_LB_RECHECK 7     /* LB re-tested against a tighter ub before DTW and skipped */
 #define EAPDTW_CNT_OVERFLOW 8       /* candidates re-run with a wider tile */
 #define EAPDTW_CNT_STEPS 9          /* warp wavefront steps executed */
