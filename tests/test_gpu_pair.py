@@ -97,3 +97,14 @@ def test_wide_live_region(n, m, w):
     assert dist_close(got, d, max(n, m)), (got, d)
     got2 = api.eap_dtw(dev(S), dev(T), w, d * 1.01).item()
     assert dist_close(got2, d, max(n, m))
+
+
+def test_lone_diagonal_path_is_not_abandoned():
+    """S = T = 0, 1, 2, ...: only the diagonal is within ub = 0.5 (every other
+    cell costs at least 1), so the live region is one cell wide and crosses
+    every block boundary diagonally; the wavefront must not take such a
+    crossing for a dead row."""
+    for m in (33, 50, 70, 100, 300, 1000):
+        S = np.arange(m, dtype=np.float32)
+        for w in (m, 10, 3):
+            assert api.eap_dtw(dev(S), dev(S), w=w, ub=0.5).item() == 0.0, (m, w)
