@@ -16,7 +16,7 @@ from paper_2010_05371_gb300 import synth
 CORNER = 16
 
 
-def corner_dead_row(z, q, ub, w):
+def corner_dead_row(z, q, ub, w, absolute=False):
     """The first corner row r that makes the rule fire, or 0."""
     D = np.full((CORNER + 1, CORNER + 1), np.inf)
     D[0, 0] = 0.0
@@ -25,7 +25,8 @@ def corner_dead_row(z, q, ub, w):
         for c in range(1, CORNER + 1):
             if abs(r - c) > w:
                 continue
-            D[r, c] = (z[r - 1] - q[c - 1]) ** 2 + min(D[r - 1, c], D[r - 1, c - 1], D[r, c - 1])
+            d = z[r - 1] - q[c - 1]
+            D[r, c] = (abs(d) if absolute else d * d) + min(D[r - 1, c], D[r - 1, c - 1], D[r, c - 1])
         edge = edge and D[r, CORNER] > ub
         if edge and np.all(D[r, 1:] > ub):
             return r
@@ -60,3 +61,19 @@ def test_rule_never_fires_on_the_nearest_neighbour():
     idx, dist = O.search_brute(Q, R, w, 1)
     z = O.znorm(R[idx[0]:idx[0] + m])
     assert corner_dead_row(z, O.znorm(Q), float(dist[0]), w) == 0
+
+
+@pytest.mark.parametrize("m,w", [(64, 64), (100, 20)])
+def test_caught_windows_exceed_ub_under_the_absolute_cost(m, w):
+    """The same rule with cost |a - b| (any non-negative cost keeps the argument)."""
+    R = synth.random_walk(40_000, 60 + m)
+    zq = O.znorm(synth.random_walk(m, 61 + m))
+    rng = np.random.default_rng(m)
+    caught = 0
+    for ub in (3.0, 10.0, 30.0):
+        for i in rng.integers(0, len(R) - m, 100):
+            z = O.znorm(R[i:i + m])
+            if corner_dead_row(z, zq, ub, w, absolute=True):
+                caught += 1
+                assert O.dtw_cost(z, zq, w, O.COST_ABSOLUTE) > ub, (i, ub)
+    assert caught >= 30, caught
