@@ -451,16 +451,24 @@ __device__ __forceinline__ DtwOut dtw_warp(const float* __restrict__ rows, float
 // grows to the right, and a later cell right of the corner has only dead
 // inputs.  So all of row r is > ub, and Algorithm 3 abandons the window.
 // Needs m >= kCorner and every corner cell inside the band (w >= kCorner - 1).
-constexpr int kCorner = 16;
+// The corner's size is a compile-time knob for tuning experiments.  Up to 16
+// columns the query values sit in registers; a wider corner reads them from
+// memory at each cell, since the registers would spill.
+#ifndef EAPDTW_CORNER
+#define EAPDTW_CORNER 16
+#endif
+constexpr int kCorner = EAPDTW_CORNER;
+static_assert(kCorner >= 2 && kCorner <= 32, "corner of 2 to 32 rows and columns");
+constexpr bool kCornerQInRegs = kCorner <= 16;
 constexpr int kCornerMinLanes = 8;   // run it only when this many lanes are alive
 
 template <int COST>
 __device__ __forceinline__ bool corner_dead(const float* x, float a, float cw, float isd, const float* zq, float ub) {
     const float INF = f_inf();
-    float q[kCorner], prv[kCorner];
+    float q[kCornerQInRegs ? kCorner : 1], prv[kCorner];
 #pragma unroll
     for (int c = 0; c < kCorner; ++c) {
-        q[c] = zq[c];
+        if (kCornerQInRegs) q[kCornerQInRegs ? c : 0] = zq[c];
         prv[c] = INF;   // row 0
     }
     bool edge = true;   // column kCorner > ub in every row so far
@@ -471,7 +479,7 @@ __device__ __forceinline__ bool corner_dead(const float* x, float a, float cw, f
 #pragma unroll
         for (int c = 0; c < kCorner; ++c) {
             const float top = prv[c];
-            const float d = __fsub_rn(z, q[c]);
+            const float d = __fsub_rn(z, kCornerQInRegs ? q[kCornerQInRegs ? c : 0] : zq[c]);
             const float mn = fmin3(top, diag, left);
             const float v = (COST == kCostAbsolute) ? __fadd_rn(fabsf(d), mn) : __fmaf_rn(d, d, mn);
             diag = top;
