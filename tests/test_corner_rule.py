@@ -13,7 +13,7 @@ import pytest
 import oracle as O
 from paper_2010_05371_gb300 import synth
 
-CORNER = 16
+CORNER = 16   # the kernel's default corner size (EAPDTW_CORNER)
 
 
 def corner_dead_row(z, q, ub, w, absolute=False):
