@@ -209,6 +209,27 @@ int32_t eapdtw_release_scratch(void);
 int32_t subseq_search_noalloc(const float* Q, int64_t lQ, const float* R, int64_t lR, int64_t w,
                               int32_t k, int64_t* out_idx, double* out_dist, void* stream);
 
+/*
+ * eapdtw_cell_peak - measured throughput ceiling of the DP cell (a measurement
+ * utility; the paper has no counterpart).
+ *
+ * Runs the cell of Eq. 1-5 (d = q - z, v = d * d + min(top, diag, left) in
+ * FP32) with nothing else around it, on every SM of the current device, and
+ * returns the fastest of three timed launches (CUDA events, after one
+ * warm-up) as DP cells per second.  It bounds what any schedule of the same
+ * cells can reach, and is the roofline denominator of the search kernels.
+ *   mode 0: scalar operations, one row per step (3 issue slots per cell);
+ *   mode 1: the subtractions of adjacent columns paired in packed f32x2 adds;
+ *   mode 2: two rows per step, anti-diagonal cell pairs in packed f32x2 adds
+ *           and fused multiply-adds;
+ *   mode 3: mode 2 with two independent blocks per thread.
+ *   steps     rows per thread, even, >= 2 (2^18 takes about 50 ms per launch).
+ *   *cells_per_s  receives the rate; *ms (optional) the launch time.
+ * Blocking; allocates and frees a small result buffer.
+ * Errors: INVALID_ARG (bad mode or steps), CUDA.
+ */
+int32_t eapdtw_cell_peak(int32_t mode, int64_t steps, double* cells_per_s, double* ms);
+
 /* ------------------------------------------------------------------------
  * Contexts and the batched search.
  *

@@ -8,7 +8,10 @@ LB_Keogh EQ -> EC -> EAPrunedDTW) and with w = 1024 (unconstrained, no lower
 bounds).  For every search this script records, from the oracle only:
   - the nearest window (index, distance) of the FP64 cascade search;
   - the EAPrunedDTW cells of an audit-mode search whose ub is fixed at that
-    distance (the work the method itself must do; order-independent).
+    distance (the work the method itself must do; order-independent);
+  - with --add-top K (run on an existing file), the K nearest windows of the
+    FP64 search, so that a GPU answer at another index can be checked for tie
+    equivalence against the oracle's own distance at that index.
 It calls nothing but oracle/ and the seeded generators; it takes tens of
 minutes on 8 cores.
 
@@ -40,8 +43,21 @@ def main():
     ap.add_argument("--threads", type=int, default=os.cpu_count() or 8)
     ap.add_argument("--n", type=int, default=20_000_000)
     ap.add_argument("--out", default=OUT)
+    ap.add_argument("--add-top", type=int, default=0,
+                    help="add the K nearest windows of every search to an existing file")
     args = ap.parse_args()
     R = synth.random_walk(args.n, 0)
+    if args.add_top:
+        with open(args.out) as f:
+            res = json.load(f)
+        for entry in res["searches"]:
+            Q = synth.random_walk(entry["m"], entry["query_seed"])
+            idx, dist, _ = O.search_cascade(Q, R, entry["w"], args.add_top, use_lb=True, nthreads=args.threads)
+            entry["top"] = [[int(i), float(d)] for i, d in zip(idx, dist)]
+            print(json.dumps({"query_seed": entry["query_seed"], "w": entry["w"], "top": entry["top"]}), flush=True)
+            with open(args.out, "w") as f:
+                json.dump(res, f, indent=1)
+        return
     res = {"workload": f"random walk n={args.n} seed 0; queries: random walks m=1024 seeds 1-4",
            "generator": "numpy default_rng(seed), cumsum of standard normals, rounded to FP32",
            "searches": []}

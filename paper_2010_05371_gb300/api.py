@@ -100,6 +100,8 @@ def lib():
         L.eapdtw_release_scratch.argtypes = []
         L.subseq_search_noalloc.restype = i32
         L.subseq_search_noalloc.argtypes = [vp, i64, vp, i64, i64, i32, vp, vp, vp]
+        L.eapdtw_cell_peak.restype = i32
+        L.eapdtw_cell_peak.argtypes = [i32, i64, C.POINTER(dbl), C.POINTER(dbl)]
         pi32 = C.POINTER(i32)
         L.eapdtw_ctx_create.restype = i32
         L.eapdtw_ctx_create.argtypes = [i32, i64, C.POINTER(vp)]
@@ -276,6 +278,13 @@ def subseq_search_noalloc(Q, R, w: int, idx, dist, stream=None):
                                      C.c_void_p(dist.data_ptr()), _stream_ptr(stream))
     _check(rc, "subseq_search_noalloc")
     return idx, dist
+
+
+def cell_peak(mode: int, steps: int = 1 << 18):
+    """Measured DP-cell throughput ceiling (eapdtw_cell_peak): (cells/s, ms)."""
+    rate, ms = C.c_double(), C.c_double()
+    _check(lib().eapdtw_cell_peak(int(mode), int(steps), C.byref(rate), C.byref(ms)), "eapdtw_cell_peak")
+    return rate.value, ms.value
 
 
 def _series_2d(X, name):

@@ -50,9 +50,10 @@
 //  * Columns past the end (c > nc) hold NaN: fminf ignores NaN operands, so
 //    such cells act as +inf and never count as alive.
 //
-// Arithmetic: each cell is fma(d, d, min(top, diag, left)) with d = z - q in
-// FP32; min is exact, so every alive cell equals the sequential FP32 DP value
-// regardless of the order in which cells are computed.
+// Arithmetic: each cell is fma(d, d, min(top, diag, left)) with d = q - z in
+// FP32 (two adjacent columns per packed f32x2 add); min is exact, so every
+// alive cell equals the sequential FP32 DP value regardless of the order in
+// which cells are computed.
 #pragma once
 
 #include "common.cuh"
@@ -207,17 +208,27 @@ __device__ __forceinline__ DtwOut dtw_warp(const float* __restrict__ rows, float
             kf = (static_cast<unsigned>(f1) < static_cast<unsigned>(K)) ? f1 : f2;
             kf2 = f2;
         }
+        // d = q - z for two adjacent columns per packed f32x2 add; the cost
+        // squares d or takes its absolute value, so the sign is immaterial and
+        // fl(q - z) = -fl(z - q) gives the scalar form's values exactly.
+        const float2 nz = make_float2(-z, -z);
 #pragma unroll
-        for (int k = 0; k < K; ++k) {
-            const float top = prv[j][k];
-            const float d = __fsub_rn(z, CS ? qs[CS ? k : 0] : zc[CS ? 0 : j][k]);
-            const float mn = fmin3(top, diag, left);
-            float v = (COST == kCostAbsolute) ? __fadd_rn(fabsf(d), mn) : __fmaf_rn(d, d, mn);
-            if (BAND == 1) v = (k == kf) ? INF : v;
-            if (BAND == 2) v = (k == kf || k == kf2) ? INF : v;
-            diag = top;
-            left = v;
-            prv[j][k] = v;
+        for (int k = 0; k < K; k += 2) {
+            const float2 dd = __fadd2_rn(CS ? make_float2(qs[CS ? k : 0], qs[CS ? k + 1 : 0])
+                                            : make_float2(zc[CS ? 0 : j][k], zc[CS ? 0 : j][k + 1]),
+                                         nz);
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                const float top = prv[j][k + u];
+                const float d = u ? dd.y : dd.x;
+                const float mn = fmin3(top, diag, left);
+                float v = (COST == kCostAbsolute) ? __fadd_rn(fabsf(d), mn) : __fmaf_rn(d, d, mn);
+                if (BAND == 1) v = (k + u == kf) ? INF : v;
+                if (BAND == 2) v = (k + u == kf || k + u == kf2) ? INF : v;
+                diag = top;
+                left = v;
+                prv[j][k + u] = v;
+            }
         }
         lout[j] = prv[j][K - 1];
         lprev[j] = lin;
@@ -458,7 +469,7 @@ __device__ __forceinline__ DtwOut dtw_warp(const float* __restrict__ rows, float
 #define EAPDTW_CORNER 16
 #endif
 constexpr int kCorner = EAPDTW_CORNER;
-static_assert(kCorner >= 2 && kCorner <= 32, "corner of 2 to 32 rows and columns");
+static_assert(kCorner >= 2 && kCorner <= 32 && kCorner % 2 == 0, "corner of 2 to 32 rows and columns, even");
 constexpr bool kCornerQInRegs = kCorner <= 16;
 constexpr int kCornerMinLanes = 8;   // run it only when this many lanes are alive
 
@@ -476,15 +487,22 @@ __device__ __forceinline__ bool corner_dead(const float* x, float a, float cw, f
         const float z = znorm1(x[r], a, cw, isd);
         float diag = r == 0 ? 0.0f : INF;   // D(0, 0) = 0; D(r, 0) = +inf
         float left = INF;
+        const float2 nz = make_float2(-z, -z);   // packed d = q - z, as in dtw_warp
 #pragma unroll
-        for (int c = 0; c < kCorner; ++c) {
-            const float top = prv[c];
-            const float d = __fsub_rn(z, kCornerQInRegs ? q[kCornerQInRegs ? c : 0] : zq[c]);
-            const float mn = fmin3(top, diag, left);
-            const float v = (COST == kCostAbsolute) ? __fadd_rn(fabsf(d), mn) : __fmaf_rn(d, d, mn);
-            diag = top;
-            left = v;
-            prv[c] = v;
+        for (int c = 0; c < kCorner; c += 2) {
+            const float2 dd = __fadd2_rn(kCornerQInRegs ? make_float2(q[kCornerQInRegs ? c : 0], q[kCornerQInRegs ? c + 1 : 0])
+                                                        : make_float2(zq[c], zq[c + 1]),
+                                         nz);
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                const float top = prv[c + u];
+                const float d = u ? dd.y : dd.x;
+                const float mn = fmin3(top, diag, left);
+                const float v = (COST == kCostAbsolute) ? __fadd_rn(fabsf(d), mn) : __fmaf_rn(d, d, mn);
+                diag = top;
+                left = v;
+                prv[c + u] = v;
+            }
         }
         float rmin = prv[0];
 #pragma unroll
