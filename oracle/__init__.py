@@ -313,7 +313,7 @@ def _bind_f32(L):
     L.o7_dtw_f32.argtypes = [_F, _F, C.c_int64, C.c_int64]
     L.o7_search.restype = C.c_int
     L.o7_search.argtypes = [_F, C.c_int64, _F, C.c_int64, C.c_int64, C.c_int, C.c_int, C.c_float, C.c_int,
-                            _I64, _I64, _D]
+                            _I64, _I64, _D, C.POINTER(C.c_int8)]
     return L
 
 
@@ -402,17 +402,23 @@ def o7_dtw_f32(z, q, w: int, L=None) -> float:
     return float((L or lib_f32()).o7_dtw_f32(_pf(z), _pf(q), len(z), int(w)))
 
 
-def o7_search(Q, R, w: int, k: int = 1, audit_ub: float | None = None, use_lb: bool = True, L=None):
+def o7_search(Q, R, w: int, k: int = 1, audit_ub: float | None = None, use_lb: bool = True, L=None,
+              return_why: bool = False):
     """FP32-emulated search: exact top-k (audit_ub None) or the audit cascade under
-    the fixed bound audit_ub.  Returns (idx, dist, counters dict)."""
+    the fixed bound audit_ub.  Returns (idx, dist, counters dict), plus with
+    return_why each window's outcome (int8: 1 LB_Kim, 2 LB_Keogh EQ, 3 LB_Keogh
+    EC, 4 abandoned, 5 completed)."""
     Q, R = _f32(Q), _f32(R)
     idx = np.empty(k, dtype=np.int64)
     dist = np.empty(k)
     cnt = np.zeros(6, dtype=np.int64)
     audit = audit_ub is not None
+    why = np.zeros(len(R) - len(Q) + 1, dtype=np.int8) if return_why else None
     rc = (L or lib_f32()).o7_search(_pf(Q), len(Q), _pf(R), len(R), int(w), int(k), int(audit),
                                     C.c_float(float(audit_ub) if audit else 0.0), int(bool(use_lb)),
-                                    cnt.ctypes.data_as(_I64), idx.ctypes.data_as(_I64), _p(dist))
+                                    cnt.ctypes.data_as(_I64), idx.ctypes.data_as(_I64), _p(dist),
+                                    why.ctypes.data_as(C.POINTER(C.c_int8)) if return_why else None)
     if rc != 0:
         raise ValueError("o7_search: invalid arguments")
-    return idx, dist, dict(zip(O7_COUNTER_NAMES, (int(c) for c in cnt)))
+    out = (idx, dist, dict(zip(O7_COUNTER_NAMES, (int(c) for c in cnt))))
+    return out + (why,) if return_why else out

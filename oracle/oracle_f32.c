@@ -364,10 +364,13 @@ static void topk_put(o7_topk* t, float d, int64_t i) {
  *     none), else its DTW completes if <= ub and is abandoned otherwise.
  *     counters: windows, LB_Kim, LB_Keogh EQ, LB_Keogh EC prunes, abandoned,
  *     completed; the k-best list is over the completed windows.
+ *   why (optional, nw entries): each window's outcome, 1 LB_Kim, 2 LB_Keogh
+ *     EQ, 3 LB_Keogh EC (pruned), 4 abandoned, 5 completed (audit), or 5
+ *     (exact mode: every window's DTW is computed).
  * Returns 0, or -1 on invalid arguments.
  * ------------------------------------------------------------------------ */
 int o7_search(const float* Q, int64_t m, const float* R, int64_t n, int64_t w, int k, int audit, float ub,
-              int use_lb, int64_t* counters, int64_t* idx, double* dist) {
+              int use_lb, int64_t* counters, int64_t* idx, double* dist, int8_t* why) {
     if (!Q || !R || m < 1 || n < m || w < 0 || k < 1 || k > 64) return -1;
     const int64_t nch = (n + O7_CHUNK - 1) / O7_CHUNK;
     const int64_t nw = n - m + 1;
@@ -418,6 +421,7 @@ int o7_search(const float* Q, int64_t m, const float* R, int64_t n, int64_t w, i
             }
             if (kim > ub_lb) {
                 ++cnt[1];
+                if (why) why[i] = 1;
                 continue;
             }
             float s = 0.0f;
@@ -428,6 +432,7 @@ int o7_search(const float* Q, int64_t m, const float* R, int64_t n, int64_t w, i
             }
             if (s > ub_lb) {
                 ++cnt[2];
+                if (why) why[i] = 2;
                 continue;
             }
             float s2 = 0.0f;
@@ -439,11 +444,13 @@ int o7_search(const float* Q, int64_t m, const float* R, int64_t n, int64_t w, i
             }
             if (s2 > ub_lb) {
                 ++cnt[3];
+                if (why) why[i] = 3;
                 continue;
             }
         }
         for (int64_t r = 0; r < m; ++r) z[r] = znorm1(R[i + r], a, cw, isd);
         const float d = o7_dtw_f32(z, zq, m, wi);
+        if (why) why[i] = (audit && !(d <= ub)) ? 4 : 5;
         if (audit) {
             if (d <= ub) {
                 ++cnt[5];

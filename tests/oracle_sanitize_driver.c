@@ -33,7 +33,7 @@ double orc_dtw_cost(const double*, int64_t, const double*, int64_t, int64_t, int
 int orc_search_brute_cost(const double*, int64_t, const double*, int64_t, int64_t, int32_t, int, int64_t*, double*);
 float o7_rsqrt_rn(float);
 int o7_search(const float*, int64_t, const float*, int64_t, int64_t, int, int, float, int, int64_t*, int64_t*,
-              double*);
+              double*, int8_t*);
 
 static uint64_t st = 88172645463325252ull;
 static double rnd(void) {
@@ -82,9 +82,11 @@ int main(void) {
     orc_search_cascade(R + 10, 40, R, N, 40, 1, 0, 9.0, 2, idx, dist, cnt);
     orc_search_brute_cost(R + 10, 40, R, 2000, 5, 2, 1, idx, dist);
     for (int i = 1; i < 2000; ++i) o7_rsqrt_rn((float)(i * 0.37));
-    o7_search(Rf + 10, 64, Rf, N, 6, 3, 0, 0.0f, 1, c6, idx, dist);
-    o7_search(Rf + 10, 64, Rf, N, 6, 3, 1, 30.0f, 1, c6, idx, dist);
-    o7_search(Rf + 10, 5000, Rf, 5001, 5000, 1, 1, 1e9f, 0, c6, idx, dist);
+    int8_t* why = (int8_t*)malloc((size_t)N);
+    o7_search(Rf + 10, 64, Rf, N, 6, 3, 0, 0.0f, 1, c6, idx, dist, NULL);
+    o7_search(Rf + 10, 64, Rf, N, 6, 3, 1, 30.0f, 1, c6, idx, dist, why);
+    o7_search(Rf + 10, 5000, Rf, 5001, 5000, 1, 1, 1e9f, 0, c6, idx, dist, why);
+    free(why);
     free(R); free(Rf); free(mus); free(sds);
     printf("ok\n");
     return 0;
