@@ -44,7 +44,7 @@ extern "C" {
 #define EAPDTW_ERR_NAN_INPUT -2     /* a NaN or Inf in an input series */
 #define EAPDTW_ERR_OUT_OF_MEMORY -3 /* scratch allocation failed */
 #define EAPDTW_ERR_CUDA -4          /* a CUDA runtime call failed */
-#define EAPDTW_ERR_TIMEOUT -5       /* a device-side wait exceeded its budget */
+#define EAPDTW_ERR_TIMEOUT -5       /* reserved: no call of this build waits on the device with a budget */
 #define EAPDTW_ERR_UNSUPPORTED -6   /* size beyond what this build supports (see each call) */
 #define EAPDTW_ERR_INTERNAL -7      /* a device-side consistency check failed */
 #define EAPDTW_ERR_BUSY -8          /* the object is in use (a reference read by the serving loop; a second server) */
@@ -189,15 +189,19 @@ int32_t eapdtw_release_scratch(void);
  * same arguments and results, but it allocates nothing, on the device or the
  * host.  Its scratch memory (window statistics, envelopes, query staging,
  * best-so-far state, work lists) is one fixed array in the library's device
- * memory, EAPDTW_NOALLOC_SCRATCH_BYTES long, which every GPU that loads the
- * library keeps until the process exits.
+ * memory, EAPDTW_NOALLOC_SCRATCH_BYTES long, which every GPU on which the
+ * entry point has been called keeps until the process exits.
  *
  *   Limits: lR <= EAPDTW_NOALLOC_MAX_N, lQ <= EAPDTW_MAX_QUERY,
  *           k <= EAPDTW_MAX_K.  Larger sizes return EAPDTW_ERR_UNSUPPORTED
  *           and launch nothing.
  *   Pointers, stream and blocking behaviour are those of subseq_search.
  *   The first call on a device looks up the array's device address on that
- *   device; make that first call before any stream capture.
+ *   device.  With CUDA's default lazy module loading, that is also when the
+ *   array's device memory is committed, so the first call on each device can
+ *   fail with EAPDTW_ERR_CUDA for lack of memory.  Make that first call at
+ *   start-up, before any phase that must not allocate and before any stream
+ *   capture; later calls commit nothing.
  *   All calls share the one array, and each call leaves its contents behind;
  *   the call clears what must start from zero itself.  Calls are serialised
  *   on the host, and each returns only after its work is done; two calls that

@@ -46,6 +46,8 @@ SPLIT_UNITS = {
                               for c in (0, 1) for j in (2, 4) for b in (0, 1, 2)],
     "batch_wide.cu": [[]] + [[f"-DEAPDTW_UNIT_JW={j}", f"-DEAPDTW_UNIT_BAND={b}"] for j in (2, 4) for b in (0, 1, 2)],
     "pair_kernel.cu": [[], ["-DEAPDTW_UNIT_PAIR_WIDE"]],
+    "search_k.cu": [[f"-DEAPDTW_UNIT_K={k}"] for k in (32, 16, 8, 4)],
+    "batch_k.cu": [[f"-DEAPDTW_UNIT_K={k}"] for k in (32, 16, 8, 4)],
 }
 
 
@@ -88,7 +90,7 @@ def build(force: bool = False, verbose_ptxas: bool = False, jobs: int | None = N
         objs.append(obj)
         cmds.append(common + defs + ["-c", src, "-o", obj])
     # the longest units first, so that they do not finish last
-    order = {"search_wide": 0, "batch_wide": 1, "pair_kernel": 2, "search_k32": 3, "search_k16": 4}
+    order = {"search_wide": 0, "batch_wide": 1, "search_k": 2, "pair_kernel": 3, "search_elastic": 4, "batch_k": 5}
     cmds.sort(key=lambda c: order.get(os.path.basename(c[-1]).split(".")[0], 9))
 
     def run(cmd):

@@ -12,13 +12,13 @@
 
 #include "eapdtw.h"
 #include "kernels.h"
+#include "plan.h"
 #include "search_kernel.cuh"
 
 using namespace eapdtw;
 
 namespace {
 
-constexpr int kMaxLevels = 4;
 constexpr int kSeedSamples = 4096;
 constexpr int kSeedBest = 32;
 constexpr float kLbScale = 1.0001f;   // prune iff lb > ub * kLbScale (FP32 rounding margin)
@@ -29,54 +29,6 @@ constexpr float kLbScale = 1.0001f;   // prune iff lb > ub * kLbScale (FP32 roun
 // and re-running a window costs its partial first run on top of the wider run).
 constexpr int kProbeSamples = 2048;
 constexpr double kProbeRate = 0.05;
-
-// Work levels: the first launch uses K cells per lane; windows whose live
-// region overflows the warp's window of 32 blocks are re-run with 2K, up to 32.
-struct Plan {
-    int nlev = 0;
-    int K[kMaxLevels + 1];
-    int band[kMaxLevels + 1];
-    bool wide[kMaxLevels + 1];
-};
-
-Plan plan_levels(int64_t nr, int64_t nc, int64_t w, int tile_hint) {
-    const int64_t lmax = nr > nc ? nr : nc;
-    const bool unconstrained = w >= lmax - 1;
-    int k0 = 32;
-    if (tile_hint == 4 || tile_hint == 8 || tile_hint == 16 || tile_hint == 32) {
-        k0 = tile_hint;
-    } else if (!unconstrained) {
-        // blocks spanned by the band across the pipelined rows, plus margin
-        for (int K = 4; K <= 32; K *= 2)
-            if ((2 * w + K) / (K + 1) + 3 <= 32) { k0 = K; break; }
-    } else {
-        k0 = 8;
-        for (int K = 4; K <= 8; K *= 2)
-            if (32 * K >= nc) { k0 = K; break; }
-    }
-    Plan p;
-    int covered = 0;  // columns of the widest window of the previous level
-    for (int K = k0; K <= 32; K *= 2) {
-        const int band = unconstrained ? 0 : (K <= 2 * w + 2 ? 1 : 2);
-        const int cols = 32 * K * dtw_windows(K, band);
-        if (cols <= covered) continue;
-        p.K[p.nlev] = K;
-        p.band[p.nlev] = band;
-        p.wide[p.nlev] = false;
-        ++p.nlev;
-        covered = cols;
-    }
-    // Last level: four windows of 32-column blocks (4096 columns), needed only
-    // when the columns do not fit one window of K = 32 (an empty re-run list
-    // makes it a no-op launch).
-    if (nc > 32 * 32) {
-        p.K[p.nlev] = 32;
-        p.band[p.nlev] = unconstrained ? 0 : (32 <= 2 * w + 2 ? 1 : 2);
-        p.wide[p.nlev] = true;
-        ++p.nlev;
-    }
-    return p;
-}
 
 float ub_to_f32_up(double ub) {
     if (std::isinf(ub)) return ub > 0 ? INFINITY : -INFINITY;
@@ -127,19 +79,6 @@ struct Scratch {
     int* ints() { return reinterpret_cast<int*>(state + 768); }
     float* ub_seed() { return reinterpret_cast<float*>(state + 896); }
 };
-
-enum IntSlot : int {
-    kWork0 = 0,      // work counters of levels 0..kMaxLevels
-    kWorkSeed = kWork0 + kMaxLevels + 1,
-    kOvf0 = kWorkSeed + 1,  // overflow counts written by levels 0..kMaxLevels
-    kBad = kOvf0 + kMaxLevels + 1,
-    kNBest = kBad + 1,
-    kSeedOvf = kNBest + 1,
-    kWorkTail = kSeedOvf + 1,     // probe: entries of the sample list; kWorkTail + 1: its work counter
-    kProbeCount = kWorkTail + 2,  // overflows among the probe's windows
-    kNumInts = 32
-};
-static_assert(kProbeCount < 24, "int slots (24.. hold the device self-check record)");
 
 // (Re)allocate p with room for n elements (previous contents are dropped).
 template <typename T>
@@ -219,7 +158,9 @@ int32_t search_impl(Scratch& S, const float* Q, int64_t lQ, const float* R, int6
     const bool audit = opts && opts->audit;
     if (audit && std::isnan(opts->ub_fixed)) return EAPDTW_ERR_INVALID_ARG;
     if (search_warps(m) < 1) return EAPDTW_ERR_UNSUPPORTED;
-    const Plan plan = plan_levels(m, m, wi, opts ? opts->tile : 0);
+    const bool tighten_req = use_lb && opts && opts->tighten;
+    // the elastic first level does not implement upper-bound tightening
+    const Plan plan = plan_levels(m, m, wi, opts ? opts->tile : 0, !tighten_req);
 
     // scratch
     if (S.cap_n < n) {
@@ -291,7 +232,7 @@ int32_t search_impl(Scratch& S, const float* Q, int64_t lQ, const float* R, int6
     a.use_lb = use_lb ? 1 : 0;
     a.lb_scale = kLbScale;
     a.counters = S.counters();
-    a.dbg = ints + 24;
+    a.dbg = ints + kDbgSlot;
     a.cb = tighten ? S.cb : nullptr;
     a.cb_stride = cb_stride;
 
@@ -319,7 +260,7 @@ int32_t search_impl(Scratch& S, const float* Q, int64_t lQ, const float* R, int6
         launches += 3;
     }
     CK(cudaEventRecord(S.ev[2], st));
-    const bool probe = !(opts && opts->tile) && plan.nlev >= 2 && !plan.wide[0] && !plan.wide[1] &&
+    const bool probe = !(opts && opts->tile) && plan.nlev >= 2 && !plan.elastic[0] && !plan.wide[0] && !plan.wide[1] &&
                        nw >= 256 * static_cast<int64_t>(kProbeSamples);
     int64_t probe_ovf = -1;
     int first_tile = plan.K[0];
@@ -337,6 +278,8 @@ int32_t search_impl(Scratch& S, const float* Q, int64_t lQ, const float* R, int6
         const bool lb = use_lb && lev == 0;
         if (plan.wide[lev]) {
             CK(launch_search_wide(plan.band[lev], la, search_blocks_wide(plan.band[lev], m, cost), st, cost));
+        } else if (plan.elastic[lev]) {
+            CK(launch_search_elastic(lb, la, search_blocks_elastic(lb, m, cost), st, cost));
         } else if (lev == 0 && probe) {
             // the probe (sampled windows, single-window mode, overflows only
             // counted), then the first level at the planned or the next width:
@@ -410,8 +353,8 @@ int32_t search_impl(Scratch& S, const float* Q, int64_t lQ, const float* R, int6
         opts->counters[EAPDTW_CNT_FIRST_TILE] = first_tile;
     }
 #ifdef EAPDTW_DEVICE_CHECKS
-    if (hi[24]) {
-        fprintf(stderr, "eapdtw device check failed: code %d value %d\n", hi[24], hi[25]);
+    if (hi[kDbgSlot]) {
+        fprintf(stderr, "eapdtw device check failed: code %d value %d\n", hi[kDbgSlot], hi[kDbgSlot + 1]);
         return EAPDTW_ERR_INTERNAL;
     }
 #endif
@@ -442,7 +385,7 @@ const char* eapdtw_strerror(int32_t code) {
         case EAPDTW_ERR_NAN_INPUT: return "NaN or Inf in an input series";
         case EAPDTW_ERR_OUT_OF_MEMORY: return "out of device memory";
         case EAPDTW_ERR_CUDA: return "CUDA runtime error";
-        case EAPDTW_ERR_TIMEOUT: return "device wait timed out";
+        case EAPDTW_ERR_TIMEOUT: return "reserved (device wait timed out)";
         case EAPDTW_ERR_UNSUPPORTED: return "size not supported by this build";
         case EAPDTW_ERR_INTERNAL: return "internal consistency check failed";
         case EAPDTW_ERR_BUSY: return "in use";
@@ -475,7 +418,7 @@ int32_t eap_dtw(const float* S, int64_t lS, const float* T, int64_t lT, int64_t 
     }
     const int64_t lmax = nr;
     const int wi = static_cast<int>(w < lmax ? w : lmax);
-    const Plan plan = plan_levels(nr, nc, wi, 0);
+    const Plan plan = plan_levels(nr, nc, wi, 0, false);   // the pair kernel's levels
     const float ubf = ub_to_f32_up(ub);
     for (int lev = 0; lev < plan.nlev; ++lev)
         CK(launch_pair(plan.K[lev], plan.band[lev], plan.wide[lev], rows, static_cast<int>(nr), cols,

@@ -41,6 +41,11 @@ int search_blocks(int K, int band, bool lb, int m, bool tight = false, int cost 
 cudaError_t launch_search_wide(int band, const SearchArgs& args, int blocks, cudaStream_t s, int cost = 0);
 int search_blocks_wide(int band, int m, int cost = 0);
 
+// The unconstrained first level with the narrow-block elastic wavefront
+// (search_elastic_kernel; tile mode only).
+cudaError_t launch_search_elastic(bool lb, const SearchArgs& args, int blocks, cudaStream_t s, int cost = 0);
+int search_blocks_elastic(bool lb, int m, int cost = 0);
+
 // eap_dtw single pair: one warp; wide selects the four-window level.
 cudaError_t launch_pair(int K, int band, bool wide, const float* rows, int nr, const float* cols, int nc,
                         int w, float ub, double* out, cudaStream_t s);

@@ -9,6 +9,7 @@
 
 #include "eapdtw.h"
 #include "kernels.h"
+#include "plan.h"
 #include "search_kernel.cuh"
 
 using namespace eapdtw;
@@ -44,8 +45,6 @@ constexpr int64_t kOffSeedBest = kOffSeedIdx + al(4 * kSeedN);
 constexpr int64_t kUsed = kOffSeedBest + al(8 * 64);
 static_assert(kUsed <= EAPDTW_NOALLOC_SCRATCH_BYTES, "scratch layout exceeds the declared size");
 
-enum : int { kWork0 = 0, kWorkSeed = 5, kOvf0 = 6, kBad = 11, kNBest = 12, kSeedOvf = 13, kInts = 32 };
-
 __device__ __align__(256) unsigned char g_scratch[EAPDTW_NOALLOC_SCRATCH_BYTES];
 
 std::mutex g_mu;
@@ -58,36 +57,6 @@ unsigned char* g_addr[64] = {nullptr};  // device address of g_scratch, per devi
             return EAPDTW_ERR_CUDA;   \
         }                             \
     } while (0)
-
-// The window of blocks per warp, as subseq_search plans it (first level K,
-// then 2K up to 32 for windows whose live region overflowed, then the
-// four-window level when the query is wider than 1024 columns).
-int plan(int m, int w, int* K, int* band, bool* wide) {
-    const bool unconstrained = w >= m - 1;
-    int k0 = 32;
-    if (!unconstrained) {
-        for (int k = 4; k <= 32; k *= 2)
-            if ((2 * w + k) / (k + 1) + 3 <= 32) { k0 = k; break; }
-    } else {
-        k0 = 8;
-        for (int k = 4; k <= 8; k *= 2)
-            if (32 * k >= m) { k0 = k; break; }
-    }
-    int n = 0;
-    for (int k = k0; k <= 32; k *= 2) {
-        K[n] = k;
-        band[n] = unconstrained ? 0 : (k <= 2 * w + 2 ? 1 : 2);
-        wide[n] = false;
-        ++n;
-    }
-    if (m > 32 * 32) {
-        K[n] = 32;
-        band[n] = unconstrained ? 0 : (32 <= 2 * w + 2 ? 1 : 2);
-        wide[n] = true;
-        ++n;
-    }
-    return n;
-}
 
 }  // namespace
 
@@ -145,12 +114,12 @@ extern "C" int32_t subseq_search_noalloc(const float* Q, int64_t lQ, const float
     long long* seed_best = reinterpret_cast<long long*>(base + kOffSeedBest);
     const int ovf_cap = static_cast<int>(nw);
 
-    int Ks[5], bands[5];
-    bool wides[5];
-    const int nlev = plan(m, wi, Ks, bands, wides);
+    // the same levels as subseq_search (plan.h)
+    const Plan plan = plan_levels(m, m, wi, 0);
+    const int nlev = plan.nlev;
 
     // the previous call's state is overwritten here: slots, counters, work lists
-    CKN(launch_init_state(slots, k, ub_seed, counters, ints, kInts, st));
+    CKN(launch_init_state(slots, k, ub_seed, counters, ints, kNumInts, st));
     CKN(cudaMemsetAsync(seed_counters, 0, 128, st));
     CKN(launch_ref_prefix(R, n, P1, P2, T1, T2, A, ints + kBad, st));
     CKN(launch_query_prep(Q, m, wi, zq, uq, lq, zqo, ord, ints + kBad, st));
@@ -181,8 +150,8 @@ extern "C" int32_t subseq_search_noalloc(const float* Q, int64_t lQ, const float
         sa.ovf_out_count = ints + kSeedOvf;
         sa.ovf_cap = 0;
         sa.counters = seed_counters;
-        const int K = Ks[nlev - 1], bd = bands[nlev - 1];
-        if (wides[nlev - 1]) {
+        const int K = plan.K[nlev - 1], bd = plan.band[nlev - 1];
+        if (plan.wide[nlev - 1]) {
             CKN(launch_search_wide(bd, sa, search_blocks_wide(bd, m) / 4 + 1, st));
         } else {
             CKN(launch_search(K, bd, false, sa, search_blocks(K, bd, false, m) / 4 + 1, st));
@@ -200,14 +169,16 @@ extern "C" int32_t subseq_search_noalloc(const float* Q, int64_t lQ, const float
             la.ovf_in_cap = ovf_cap;
         }
         const bool lb = lev == 0;
-        if (wides[lev]) {
-            CKN(launch_search_wide(bands[lev], la, search_blocks_wide(bands[lev], m), st));
+        if (plan.wide[lev]) {
+            CKN(launch_search_wide(plan.band[lev], la, search_blocks_wide(plan.band[lev], m), st));
+        } else if (plan.elastic[lev]) {
+            CKN(launch_search_elastic(lb, la, search_blocks_elastic(lb, m), st));
         } else {
-            CKN(launch_search(Ks[lev], bands[lev], lb, la, search_blocks(Ks[lev], bands[lev], lb, m), st));
+            CKN(launch_search(plan.K[lev], plan.band[lev], lb, la, search_blocks(plan.K[lev], plan.band[lev], lb, m), st));
         }
     }
     CKN(launch_finalize(slots, k, out_idx, out_dist, st));
-    int hi[kInts];
+    int hi[kNumInts];
     CKN(cudaMemcpyAsync(hi, ints, sizeof(hi), cudaMemcpyDeviceToHost, st));
     CKN(cudaStreamSynchronize(st));
     if (hi[kBad]) return EAPDTW_ERR_NAN_INPUT;

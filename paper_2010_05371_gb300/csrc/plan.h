@@ -1,0 +1,93 @@
+// The launch plan of one subsequence search, shared by subseq_search and
+// subseq_search_noalloc: which wavefront runs each level, and the slots of the
+// search's small integer state array.
+#pragma once
+
+#include <cstdint>
+
+#include "dtw_elastic.cuh"
+
+namespace eapdtw {
+
+constexpr int kMaxLevels = 4;   // levels 0..kMaxLevels (at most five: K = 4, 8, 16, 32, wide)
+
+// Work levels: the first launch runs every window; windows whose live region
+// overflowed the previous level's window of blocks are re-run by the next one,
+// up to the widest (K = 32 with several windows of columns).
+struct Plan {
+    int nlev = 0;
+    int K[kMaxLevels + 1];
+    int band[kMaxLevels + 1];
+    bool wide[kMaxLevels + 1];      // K = 32, columns streamed, two or four windows
+    bool elastic[kMaxLevels + 1];   // the narrow-block elastic wavefront (unconstrained first level)
+};
+
+// nr, nc: rows and columns of the DP (window and query lengths); w: the window
+// (w >= max(nr, nc) - 1 is unconstrained); tile_hint: 4, 8, 16 or 32 fixes the
+// first level's K, 0 chooses.  allow_elastic: the unconstrained first level
+// may use the elastic wavefront (it does not implement upper-bound tightening).
+inline Plan plan_levels(int64_t nr, int64_t nc, int64_t w, int tile_hint, bool allow_elastic = true) {
+    const int64_t lmax = nr > nc ? nr : nc;
+    const bool unconstrained = w >= lmax - 1;
+    Plan p;
+    int covered = 0;  // columns of the widest window of the previous level
+    int k0 = 32;
+    if (tile_hint == 4 || tile_hint == 8 || tile_hint == 16 || tile_hint == 32) {
+        k0 = tile_hint;
+    } else if (!unconstrained) {
+        // blocks spanned by the band across the pipelined rows, plus margin
+        for (int K = 4; K <= 32; K *= 2)
+            if ((2 * w + K) / (K + 1) + 3 <= 32) { k0 = K; break; }
+    } else if (allow_elastic && nc > 32 * 4) {
+        p.K[0] = kElK;
+        p.band[0] = 0;
+        p.wide[0] = false;
+        p.elastic[0] = true;
+        p.nlev = 1;
+        covered = 32 * kElJ * kElK;
+        k0 = 8;
+    } else {
+        k0 = 8;
+        for (int K = 4; K <= 8; K *= 2)
+            if (32 * K >= nc) { k0 = K; break; }
+    }
+    for (int K = k0; K <= 32; K *= 2) {
+        const int band = unconstrained ? 0 : (K <= 2 * w + 2 ? 1 : 2);
+        const int cols = 32 * K * dtw_windows(K, band);
+        if (cols <= covered) continue;
+        p.K[p.nlev] = K;
+        p.band[p.nlev] = band;
+        p.wide[p.nlev] = false;
+        p.elastic[p.nlev] = false;
+        ++p.nlev;
+        covered = cols;
+    }
+    // Last level: four windows of 32-column blocks (4096 columns), needed only
+    // when the columns do not fit one window of K = 32 (an empty re-run list
+    // makes it a no-op launch).
+    if (nc > 32 * 32) {
+        p.K[p.nlev] = 32;
+        p.band[p.nlev] = unconstrained ? 0 : (32 <= 2 * w + 2 ? 1 : 2);
+        p.wide[p.nlev] = true;
+        p.elastic[p.nlev] = false;
+        ++p.nlev;
+    }
+    return p;
+}
+
+// Slots of the search's int array (device).
+enum IntSlot : int {
+    kWork0 = 0,                             // work counters of levels 0..kMaxLevels
+    kWorkSeed = kWork0 + kMaxLevels + 1,
+    kOvf0 = kWorkSeed + 1,                  // overflow counts written by levels 0..kMaxLevels
+    kBad = kOvf0 + kMaxLevels + 1,
+    kNBest = kBad + 1,
+    kSeedOvf = kNBest + 1,
+    kWorkTail = kSeedOvf + 1,               // probe: entries of the sample list; kWorkTail + 1: its work counter
+    kProbeCount = kWorkTail + 2,            // overflows among the probe's windows
+    kDbgSlot = 24,                          // 24.. hold the device self-check record
+    kNumInts = 32
+};
+static_assert(kProbeCount < kDbgSlot, "int slots overlap the device self-check record");
+
+}  // namespace eapdtw

@@ -20,6 +20,7 @@
 
 #include "common.cuh"
 #include "dtw_wavefront.cuh"
+#include "dtw_elastic.cuh"
 
 namespace eapdtw {
 
@@ -102,6 +103,7 @@ struct TileCtx {
     long long tag;        // high bits of the overflow entries (batch item << 32)
     int* lost;            // set to 1 when an overflow entry did not fit the list (or nullptr)
     float* cbw;           // this warp's scratch for upper-bound tightening (>= m + 1 floats), or nullptr
+    float* zr;            // elastic wavefront: this warp's row buffer (row 1 at zr[0], NaN pads around)
     int* dbg;
 };
 
@@ -160,8 +162,10 @@ __device__ __forceinline__ void tightening_terms(const TileCtx& C, const float* 
 // 32 blocks (fewer registers per thread, more resident warps).
 // TIGHT: upper-bound tightening for the survivors (needs C.cbw and the lower
 // bounds; compiled out otherwise).
+// EL: run the survivors through the narrow-block elastic wavefront
+// (dtw_elastic.cuh; unconstrained, K = kElK, C.zr and C.zq padded as it needs).
 template <int K, int BAND, bool LB, int JW, bool STAGE = true, int ECM = 1, bool TIGHT = false, int COST = 0,
-          typename CountF>
+          bool EL = false, typename CountF>
 __device__ __forceinline__ void process_tile(const TileCtx& C, float* s_r, bool list_mode, int64_t i0,
                                              int nlanes, CountF count) {
     const int lane = threadIdx.x & 31;
@@ -326,12 +330,24 @@ __device__ __forceinline__ void process_tile(const TileCtx& C, float* s_r, bool 
             continue;
         }
         if (TIGHT) tightening_terms(C, s_r + off, a_s, cw_s, isd_s);
-        constexpr int kJ = JW > 0 ? JW : dtw_windows(K, BAND);
-        const DtwOut o = dtw_warp<K, BAND, kJ, (JW > 0), TIGHT, COST>(s_r + off, a_s, cw_s, isd_s, C.zq, m, m,
-                                                                  C.w, C.bsf, ub, C.dbg, TIGHT ? C.cbw : nullptr);
+        DtwOut o;
+        if constexpr (EL) {
+            static_assert(BAND == 0 && !TIGHT, "the elastic wavefront is unconstrained, without tightening");
+            // the window's z-normalised rows into the warp's buffer (the same
+            // znorm1 values the other wavefront computes row by row)
+            const float* xw = s_r + off;
+            for (int i = lane; i < m; i += 32) C.zr[i] = znorm1(xw[i], a_s, cw_s, isd_s);
+            __syncwarp();
+            o = dtw_elastic<kElJ, COST>(C.zr, C.zq, m, m, C.bsf, ub);
+            __syncwarp();   // every lane is done with the rows before the next survivor's
+        } else {
+            constexpr int kJ = JW > 0 ? JW : dtw_windows(K, BAND);
+            o = dtw_warp<K, BAND, kJ, (JW > 0), TIGHT, COST>(s_r + off, a_s, cw_s, isd_s, C.zq, m, m, C.w, C.bsf,
+                                                             ub, C.dbg, TIGHT ? C.cbw : nullptr);
+        }
         if (lane == 0) {
             count(kCntSteps, static_cast<unsigned long long>(o.steps));
-            count(kCntCells, static_cast<unsigned long long>(o.busy) * K);
+            count(kCntCells, static_cast<unsigned long long>(o.busy) * (EL ? kElCellsPerStep : K));
         }
         if (o.status != 0) {
             if (lane == 0) {
@@ -441,6 +457,7 @@ search_kernel(const SearchArgs A) {
     C.tag = 0;
     C.lost = nullptr;
     C.cbw = A.cb ? A.cb + (static_cast<int64_t>(blockIdx.x) * (blockDim.x >> 5) + warp) * A.cb_stride : nullptr;
+    C.zr = nullptr;
     C.dbg = A.dbg;
 
     for (;;) {
@@ -457,6 +474,111 @@ search_kernel(const SearchArgs A) {
             process_tile<K, BAND, LB, JW, true, 1, TIGHT, COST>(C, s_r, true, A.ovf_in[item] & 0xffffffffll, 1,
                                                                 count);
         }
+    }
+
+    __syncthreads();
+    if (threadIdx.x < 10 && s_cnt[threadIdx.x]) atomicAdd(A.counters + threadIdx.x, s_cnt[threadIdx.x]);
+}
+
+// ---------------------------------------------------------------------------
+// The unconstrained first level with the narrow-block elastic wavefront
+// (dtw_elastic.cuh).  Tile mode only (the re-runs of overflowed windows use
+// search_kernel's list mode).  Windows are read through L1 from the
+// reference (no staged tile); shared memory holds the query, NaN-padded past
+// its last column, the lower-bound arrays when LB, and one row buffer per warp
+// with its NaN pads.
+__host__ __device__ inline int elastic_query_floats(int m, bool lb) {
+    return elastic_col_floats(m) + (lb ? 4 * query_pad(m) : 0);
+}
+__host__ inline int elastic_warps(int m, bool lb) {
+    const size_t budget = 227 * 1024 - 1024;   // the kernel's static shared memory fits in the rest
+    const size_t q = sizeof(float) * static_cast<size_t>(elastic_query_floats(m, lb));
+    const size_t r = sizeof(float) * static_cast<size_t>(elastic_row_floats(m));
+    if (q + r > budget) return 0;
+    const size_t w = (budget - q) / r;
+    return static_cast<int>(w < kWarpsPerBlock ? w : kWarpsPerBlock);
+}
+__host__ inline size_t elastic_smem_bytes(int m, bool lb) {
+    return sizeof(float) * (static_cast<size_t>(elastic_query_floats(m, lb)) +
+                            static_cast<size_t>(elastic_warps(m, lb)) * elastic_row_floats(m));
+}
+
+#ifndef EAPDTW_MINB_ELASTIC
+#define EAPDTW_MINB_ELASTIC 3
+#endif
+template <bool LB, int COST>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32, EAPDTW_MINB_ELASTIC) search_elastic_kernel(const SearchArgs A) {
+    extern __shared__ __align__(16) float smem[];
+    const int m = A.q.m;
+    const int mp = query_pad(m);
+    const int ecf = elastic_col_floats(m);
+    const int erf = elastic_row_floats(m);
+    float* s_zq = smem;
+    float* s_uq = s_zq + ecf;
+    float* s_lq = s_uq + (LB ? mp : 0);
+    float* s_zqo = s_lq + (LB ? mp : 0);
+    int* s_ord = reinterpret_cast<int*>(s_zqo + (LB ? mp : 0));
+    const int warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
+    float* s_rows = reinterpret_cast<float*>(s_ord + (LB ? mp : 0)) + warp * erf;
+
+    __shared__ unsigned long long s_cnt[10];
+    if (threadIdx.x < 10) s_cnt[threadIdx.x] = 0;
+    for (int j = threadIdx.x; j < ecf; j += blockDim.x) s_zq[j] = j < m ? A.q.zq[j] : f_nan();
+    if (LB) {
+        for (int j = threadIdx.x; j < mp; j += blockDim.x) {
+            s_uq[j] = A.q.uq_o[j];
+            s_lq[j] = A.q.lq_o[j];
+            s_zqo[j] = A.q.zq_o[j];
+            s_ord[j] = A.q.ord[j];
+        }
+    }
+    // the row buffer's NaN pads (its rows are written per survivor)
+    for (int j = lane; j < erf; j += 32)
+        if (j < kElPadRows || j >= kElPadRows + m) s_rows[j] = f_nan();
+    __syncthreads();
+
+    const int64_t tile_lo = A.tile_lo;
+    const int64_t tile_hi = A.tile_hi > 0 ? A.tile_hi : (A.nw + 31) / 32;
+    const int64_t nitems = tile_hi - tile_lo;
+    auto count = [&](int c, unsigned long long v) { if (v) atomicAdd(s_cnt + c, v); };
+    TileCtx C;
+    C.ref = A.ref;
+    C.zq = s_zq;
+    C.uq = s_uq;
+    C.lq = s_lq;
+    C.zqo = s_zqo;
+    C.ord = s_ord;
+    C.m = m;
+    C.w = A.w;
+    C.use_lb = LB ? A.use_lb : 0;
+    C.use_ec = LB ? A.use_lb : 0;
+    C.ur = A.ur;
+    C.lr = A.lr;
+    C.eu = nullptr;
+    C.el = nullptr;
+    C.ec_w = 0;
+    C.ec_d = 0;
+    C.lb_scale = A.lb_scale;
+    C.bsf = A.bsf;
+    C.nw = A.nw;
+    C.ovf_out = A.ovf_out;
+    C.ovf_out_count = A.ovf_out_count;
+    C.ovf_cap = A.ovf_cap;
+    C.tag = 0;
+    C.lost = nullptr;
+    C.cbw = nullptr;
+    C.zr = s_rows + kElPadRows;
+    C.dbg = A.dbg;
+
+    for (;;) {
+        int item = 0;
+        if (lane == 0) item = atomicAdd(A.work_counter, 1);
+        item = __shfl_sync(kFull, item, 0);
+        if (item >= nitems) break;
+        const int64_t i0 = (tile_lo + item) * 32;
+        process_tile<kElK, 0, LB, 0, false, 1, false, COST, true>(
+            C, nullptr, false, i0, static_cast<int>(A.nw - i0 < 32 ? A.nw - i0 : 32), count);
     }
 
     __syncthreads();

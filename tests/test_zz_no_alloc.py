@@ -1,18 +1,25 @@
 """The search entry point for callers that cannot allocate memory.
 
 subseq_search_noalloc keeps its scratch in one fixed device array of the
-library instead of allocating it.  Its results must be those of subseq_search
-(the entry point that allocates its scratch), within the tolerance of the
-other GPU tests, and a second call must not be affected by what the first one
-left in the shared array.  This file is collected last so that a run stopping
-at its first failure has already run every other test.
+library instead of allocating it (for callers inside an allocator or memory
+pool they do not own, or under a no-allocation-after-start-up policy).  Each
+call's result must be the oracle's (distances within the GPU tests' tolerance;
+an index that differs must carry, in the oracle, a distance within the same
+tolerance of the best) and the allocating entry point's.  The calls run small,
+large, small, so that what a larger call left in the shared array cannot
+affect the next one, and they reach every path: the sampled seed, the
+no-seed path (fewer than 2048 windows), the widest re-run level (queries
+longer than 1024 points) and k larger than the number of windows.  This file
+is collected last so that a run stopping at its first failure has already run
+every other test.
 """
 import ctypes
 
 import numpy as np
 import pytest
 
-from gpu_util import dist_close
+import oracle as O
+from gpu_util import check_topk, dist_close
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
@@ -31,25 +38,27 @@ def _call_noalloc(Q, R, w, k):
     return idx.cpu().numpy(), dist.cpu().numpy()
 
 
-def _same(a, b, m):
-    ai, ad = a
-    bi, bd = b
-    for x, y in zip(ad, bd):
-        assert dist_close(float(x), float(y), m)
-    assert list(ai) == list(bi) or all(dist_close(float(x), float(y), m) for x, y in zip(ad, bd))
+# (reference, query, w, k); windows = len(R) - len(Q) + 1
+SMALL_1 = (synth.random_walk(2000, 21), synth.random_walk(128, 22), 13, 3)            # 1873 windows: no seed
+LARGE = (synth.random_walk(1_000_000, 23), synth.random_walk(256, 24), 26, 5)         # seeded, 999,745 windows
+SMALL_2 = (synth.random_walk(2600, 25), synth.random_walk(1100, 26), 1100, 2)         # no seed, widest level
+TINY = (synth.ecg_like(131, 27), synth.ecg_query(128, 28), 20, 6)                     # 4 windows, k = 6
 
 
-def test_noalloc_matches_allocating_entry_point_twice():
-    cases = [
-        (synth.random_walk(300_000, 21), synth.random_walk(256, 22), 26, 3),
-        (synth.ecg_like(200_000, 23), synth.ecg_query(128, 24), 13, 5),
-    ]
-    for R_np, Q_np, w, k in cases:  # two calls in a row, different inputs
+def test_noalloc_matches_the_oracle_small_large_small():
+    for R_np, Q_np, w, k in (SMALL_1, LARGE, SMALL_2, TINY, SMALL_1):
         R = torch.tensor(R_np, dtype=torch.float32, device="cuda")
         Q = torch.tensor(Q_np, dtype=torch.float32, device="cuda")
-        got = _call_noalloc(Q, R, w, k)
-        ref_i, ref_d = api.subseq_search(Q, R, w, k)
-        _same(got, (ref_i.cpu().numpy(), ref_d.cpu().numpy()), len(Q_np))
+        gi, gd = _call_noalloc(Q, R, w, k)
+        oi, od, _ = O.search_cascade(Q_np, R_np, w, k, nthreads=8)
+        check_topk(gi, gd, oi, od, Q_np, R_np, w)
+        nw = len(R_np) - len(Q_np) + 1
+        if k > nw:   # the slots past the last window
+            assert list(gi[nw:]) == [-1] * (k - nw) and np.all(np.isinf(gd[nw:]))
+        # and the allocating entry point's result
+        ri, rd = api.subseq_search(Q, R, w, k)
+        for x, y in zip(gd, rd.cpu().numpy()):
+            assert dist_close(float(x), float(y), len(Q_np))
 
 
 def test_noalloc_rejects_sizes_beyond_its_array():
