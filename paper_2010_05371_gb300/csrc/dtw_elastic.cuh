@@ -32,7 +32,8 @@
 //  * Right border (pruning_point).  Cells right of the live region are computed
 //    as dead values.  The live region grows by at most one block per step, so a
 //    window is switched on at a check when an alive block of the last active
-//    window lies within kElCE + 1 blocks of its end; when that happens with J
+//    window lies within kElCE + 1 blocks of its end (checks every kElCE
+//    steps); when that happens with J
 //    windows active the candidate overflows and is re-run wider.
 //  * Early abandoning.  Every active block dead at two consecutive steps means
 //    every later cell has dead inputs only: the result is +inf (the border
@@ -42,13 +43,31 @@
 // sequential FP32 DP value.
 #pragma once
 
+#include <type_traits>
+
 #include "dtw_wavefront.cuh"
 
 namespace eapdtw {
 
 constexpr int kElK = 4;    // columns per block
 constexpr int kElR = 2;    // rows per step
-constexpr int kElCE = 4;   // steps between checks
+// Steps between checks (a power of 2; a compile-time knob for tuning
+// experiments).  Measured on the large workload's unconstrained searches: 4
+// steps 75.9 ms, 8 steps 66.8 ms, 16 steps 97.8 ms per search (the switch-on
+// margin of CE + 1 blocks keeps more windows on as CE grows, while the checks'
+// own instructions shrink).
+#ifndef EAPDTW_ELASTIC_CE
+#define EAPDTW_ELASTIC_CE 8
+#endif
+constexpr int kElCE = EAPDTW_ELASTIC_CE;
+// 1: the anti-diagonal cell pairs (r, k), (r + 1, k - 1) share packed f32x2
+// adds and fused multiply-adds (identical values, fewer issue slots, two more
+// registers per window; 65.2 against 66.8 ms per search); 0: scalar
+// operations.  A knob for tuning experiments.
+#ifndef EAPDTW_ELASTIC_PAIRED
+#define EAPDTW_ELASTIC_PAIRED 1
+#endif
+constexpr bool kElPaired = EAPDTW_ELASTIC_PAIRED != 0;
 #ifndef EAPDTW_ELASTIC_WINDOWS
 #define EAPDTW_ELASTIC_WINDOWS 3
 #endif
@@ -69,10 +88,17 @@ __host__ __device__ inline int elastic_col_floats(int m) { return (m + kElPadCol
 // Cells one busy lane-step computes.
 constexpr int kElCellsPerStep = kElK * kElR;
 
-// zr: row r (1-based) at zr[r - 1], NaN at zr[-kElPadRows .. -1] and
+// zr: minus row r (1-based), -z_r, at zr[r - 1] (so that d = q + (-z) is one
+// add, packed or not), NaN at zr[-kElPadRows .. -1] and
 // zr[nr .. nr + kElPadRows + 2); zq: column c at zq[c - 1], NaN from zq[nc]
 // through zq[nc + kElPadCols - 1], 16-byte aligned.  All 32 lanes call it
-// with identical arguments.  Returns busy = lane-steps whose rows started.
+// with identical arguments.  Returns busy = lane-steps executed by the
+// active windows (started or not).
+//
+// The steps and the check between them are compiled once per number of
+// active windows (1..J), so that a step computes only the active windows and
+// inactive ones hold no live state: a window's state is reset when it is
+// switched on.
 template <int J, int COST>
 __device__ __forceinline__ DtwOut dtw_elastic(const float* __restrict__ zr, const float* __restrict__ zq, int nr,
                                               int nc, const BestSoFar bsf, float ub) {
@@ -82,9 +108,11 @@ __device__ __forceinline__ DtwOut dtw_elastic(const float* __restrict__ zr, cons
     const float INF = f_inf();
     float p[J][K];          // the block's values at its second row of the last step
     float q[J][K];          // its columns
+    float2 qp[kElPaired ? J : 1][kElPaired ? K - 1 : 1];   // pairs (q[k], q[k - 1]), k = 1..3
     float lo0[J], lo1[J];   // its last column at the two rows of the last step
     float dg[J];            // diagonal input of its first cell: D(r - 1, 4b)
-    int B0 = 0, jact = 1;
+    const float* zp[J];     // rows of window j at step s: zp[j] + 2 s
+    int B0 = 0, jact = 1, t = 0;
 
     auto reset = [&](int j) {
 #pragma unroll
@@ -96,11 +124,30 @@ __device__ __forceinline__ DtwOut dtw_elastic(const float* __restrict__ zr, cons
     auto load_q = [&](int j) {
         const float4 v = *reinterpret_cast<const float4*>(zq + (B0 + 32 * j + lane) * K);
         q[j][0] = v.x; q[j][1] = v.y; q[j][2] = v.z; q[j][3] = v.w;
+        if (kElPaired) {
+            qp[kElPaired ? j : 0][0] = make_float2(v.y, v.x);
+            qp[kElPaired ? j : 0][kElPaired ? 1 : 0] = make_float2(v.z, v.y);
+            qp[kElPaired ? j : 0][kElPaired ? 2 : 0] = make_float2(v.w, v.z);
+        }
     };
+    // zp[j] + 2 s points at rows 2(s-1-b)+1, +2 of block b.  The offset is
+    // capped so that for the CE steps after step tnow no block reads past the
+    // first NaN row after the last one: a block that has passed the last row
+    // reads NaN rows (at most 2 CE + 2 floats beyond it).  Unstarted blocks
+    // read the NaN rows before the first.
+    const int nre = (nr + 1) & ~1;
+    auto set_zp = [&](int tnow) {
 #pragma unroll
-    for (int j = 0; j < J; ++j) reset(j);
+        for (int j = 0; j < J; ++j) {
+            const int o = -2 * (1 + B0 + 32 * j + lane);
+            const int cap = nre - 2 * (tnow + 1);
+            zp[j] = zr + (o < cap ? o : cap);
+        }
+    };
+    reset(0);
     load_q(0);
     if (lane == 0) dg[0] = 0.0f;   // D(0, 0) = 0: diagonal of cell (1, 1)
+    set_zp(0);
 
     ub = fminf(ub, 3.402823466e38f);   // +inf cells (borders, retired blocks) are dead
     BestSoFar::Raw ub_raw = BestSoFar::of(ub);
@@ -109,199 +156,197 @@ __device__ __forceinline__ DtwOut dtw_elastic(const float* __restrict__ zr, cons
     const int t_end = bm + 1 + (nr - 1) / 2;  // step holding row nr of block bm
     const bool last_first = (nr & 1) != 0;    // row nr is the first of its step's two rows
     DtwOut out{INF, 0, 0, 0};
-    int busy = 0;
-    // Rows of window j at step s: zr + zoff[j] + 2 s, i.e. rows 2(s-1-b)+1, +2
-    // of block b.  At every check the offset is capped so that no block reads
-    // past the first NaN row after the last one for the next CE steps: a block
-    // that has passed the last row reads NaN rows (at most 2 CE + 2 floats
-    // beyond it).  Unstarted blocks read the NaN rows before the first.
-    const int nre = (nr + 1) & ~1;
-    int zoff[J];
-    auto set_zoff = [&](int tnow) {
-#pragma unroll
-        for (int j = 0; j < J; ++j) {
-            const int o = -2 * (1 + B0 + 32 * j + lane);
-            const int cap = nre - 2 * (tnow + 1);
-            zoff[j] = o < cap ? o : cap;
-        }
-    };
-    set_zoff(0);
+    int busy = 0;   // window-steps (the same on every lane)
 
-    auto cost = [&](float qv, float z, float mn) -> float {
-        const float d = __fsub_rn(qv, z);
+    // nz = -z: d = q + nz = q - z exactly
+    auto cost = [&](float qv, float nz, float mn) -> float {
+        const float d = __fadd_rn(qv, nz);
         return COST == kCostAbsolute ? __fadd_rn(fabsf(d), mn) : __fmaf_rn(d, d, mn);
     };
-    // One step of every active window.  which = 1 or 2: bma[j] or bmb[j]
-    // receives the min of the block's outputs (its second row and the first
-    // row's last column); cap >= 0 asks for row nr's column km of this lane's
-    // block of window cap >> 5, into fin.
-    float bma[J], bmb[J];
-    float fin = INF;
-    auto step = [&](int s, int which, int cap) {
-        float l0[J], l1[J];
-#pragma unroll
-        for (int j = 0; j < J; ++j) {
-            if (j < jact) {
-                const float s0 = (lane == 31) ? (j > 0 ? lo0[j > 0 ? j - 1 : 0] : INF) : lo0[j];
-                const float s1 = (lane == 31) ? (j > 0 ? lo1[j > 0 ? j - 1 : 0] : INF) : lo1[j];
-                l0[j] = __shfl_sync(kFull, s0, (lane + 31) & 31);
-                l1[j] = __shfl_sync(kFull, s1, (lane + 31) & 31);
-            }
-        }
-#pragma unroll
-        for (int j = 0; j < J; ++j) {
-            if (j < jact) {
-                const float2 zz = *reinterpret_cast<const float2*>(zr + zoff[j] + 2 * s);
-                const float z0 = zz.x, z1 = zz.y;
-                const float a0 = cost(q[j][0], z0, fmin3(p[j][0], dg[j], l0[j]));
-                const float a1 = cost(q[j][1], z0, fmin3(p[j][1], p[j][0], a0));
-                const float b0 = cost(q[j][0], z1, fmin3(a0, l0[j], l1[j]));
-                const float a2 = cost(q[j][2], z0, fmin3(p[j][2], p[j][1], a1));
-                const float b1 = cost(q[j][1], z1, fmin3(a1, a0, b0));
-                const float a3 = cost(q[j][3], z0, fmin3(p[j][3], p[j][2], a2));
-                const float b2 = cost(q[j][2], z1, fmin3(a2, a1, b1));
-                const float b3 = cost(q[j][3], z1, fmin3(a3, a2, b2));
-                if (cap >= 0 && j == (cap >> 5)) {
-                    const float ra = km == 0 ? a0 : (km == 1 ? a1 : (km == 2 ? a2 : a3));
-                    const float rb = km == 0 ? b0 : (km == 1 ? b1 : (km == 2 ? b2 : b3));
-                    fin = last_first ? ra : rb;
-                }
-                p[j][0] = b0; p[j][1] = b1; p[j][2] = b2; p[j][3] = b3;
-                lo0[j] = a3;
-                lo1[j] = b3;
-                dg[j] = l1[j];
-                if (which == 1) bma[j] = fmin3(fmin3(b0, b1, b2), b3, a3);
-                if (which == 2) bmb[j] = fmin3(fmin3(b0, b1, b2), b3, a3);
-            }
-        }
+    auto cost2 = [&](float2 qv, float2 nz, float2 mn) -> float2 {
+        const float2 d = __fadd2_rn(qv, nz);
+        if (COST == kCostAbsolute) return __fadd2_rn(make_float2(fabsf(d.x), fabsf(d.y)), mn);
+        return __ffma2_rn(d, d, mn);
     };
-    // lane-steps with started rows among steps (t0, t1] of this lane's blocks
-    auto count_busy = [&](int t0, int t1) {
-        const int half = (nr + 1) >> 1;
-#pragma unroll
-        for (int j = 0; j < J; ++j) {
-            if (j < jact) {
-                const int b = B0 + 32 * j + lane;
-                const int lo = t0 > b ? t0 : b;
-                const int hi = t1 < b + half ? t1 : b + half;
-                busy += hi > lo ? hi - lo : 0;
-            }
+    // Window j's step s given its left inputs: the two rows along
+    // anti-diagonals.  Returns the min of the block's outputs (its second row
+    // and the first row's last column); with cap, row nr's column km into fin.
+    float fin = INF;
+    auto cells = [&](int j, int s, float l0, float l1, bool cap) -> float {
+        const float2 zz = *reinterpret_cast<const float2*>(zp[j] + 2 * s);   // (-z_r, -z_r+1)
+        const float z0 = zz.x, z1 = zz.y;
+        float a0, a1, a2, a3, b0, b1, b2, b3;
+        a0 = cost(q[j][0], z0, fmin3(p[j][0], dg[j], l0));
+        if (kElPaired) {
+            const int jq = kElPaired ? j : 0;
+            float2 v = cost2(qp[jq][0], zz, make_float2(fmin3(p[j][1], p[j][0], a0), fmin3(a0, l0, l1)));
+            a1 = v.x; b0 = v.y;
+            v = cost2(qp[jq][kElPaired ? 1 : 0], zz, make_float2(fmin3(p[j][2], p[j][1], a1), fmin3(a1, a0, b0)));
+            a2 = v.x; b1 = v.y;
+            v = cost2(qp[jq][kElPaired ? 2 : 0], zz, make_float2(fmin3(p[j][3], p[j][2], a2), fmin3(a2, a1, b1)));
+            a3 = v.x; b2 = v.y;
+        } else {
+            a1 = cost(q[j][1], z0, fmin3(p[j][1], p[j][0], a0));
+            b0 = cost(q[j][0], z1, fmin3(a0, l0, l1));
+            a2 = cost(q[j][2], z0, fmin3(p[j][2], p[j][1], a1));
+            b1 = cost(q[j][1], z1, fmin3(a1, a0, b0));
+            a3 = cost(q[j][3], z0, fmin3(p[j][3], p[j][2], a2));
+            b2 = cost(q[j][2], z1, fmin3(a2, a1, b1));
         }
+        b3 = cost(q[j][3], z1, fmin3(a3, a2, b2));
+        if (cap) {
+            const float ra = km == 0 ? a0 : (km == 1 ? a1 : (km == 2 ? a2 : a3));
+            const float rb = km == 0 ? b0 : (km == 1 ? b1 : (km == 2 ? b2 : b3));
+            fin = last_first ? ra : rb;
+        }
+        p[j][0] = b0; p[j][1] = b1; p[j][2] = b2; p[j][3] = b3;
+        lo0[j] = a3;
+        lo1[j] = b3;
+        dg[j] = l1;
+        return fmin3(fmin3(b0, b1, b2), b3, a3);
+    };
+    // Left inputs of window j: lane l takes lane l-1's last column; lane 0
+    // takes lane 31's of window j-1 (+inf for window 0).  All windows' inputs
+    // are read before any window computes.
+    auto left = [&](int j, float& l0, float& l1) {
+        const bool last = lane == 31;
+        const float s0 = last ? (j > 0 ? lo0[j > 0 ? j - 1 : 0] : INF) : lo0[j];
+        const float s1 = last ? (j > 0 ? lo1[j > 0 ? j - 1 : 0] : INF) : lo1[j];
+        l0 = __shfl_sync(kFull, s0, (lane + 31) & 31);
+        l1 = __shfl_sync(kFull, s1, (lane + 31) & 31);
     };
 
-    int t = 0;   // steps completed
+    // CE steps with ja active windows, then the check.  Returns 0 to go on,
+    // 1 when every active block was dead at the last two steps (+inf), 2 on
+    // overflow.
+    auto interval = [&](auto ja) -> int {
+        constexpr int JA = decltype(ja)::value;
+        float bma[JA], bmb[JA];
+#pragma unroll
+        for (int s = 1; s <= CE; ++s) {
+            float l0[JA], l1[JA];
+#pragma unroll
+            for (int j = 0; j < JA; ++j) left(j, l0[j], l1[j]);
+#pragma unroll
+            for (int j = 0; j < JA; ++j) {
+                const float mn = cells(j, t + s, l0[j], l1[j], false);
+                if (s == CE - 1) bma[j] = mn;
+                if (s == CE) bmb[j] = mn;
+            }
+        }
+        t += CE;
+        busy += JA * CE;
+        // ---- check ----
+        ub = fminf(ub, __shfl_sync(kFull, BestSoFar::finish(ub_raw), 0));   // one reading for the warp
+        ub_raw = bsf.issue();
+        unsigned da[JA], db[JA];
+        bool all_dead = true;
+        int hi = -1;   // highest block (relative to B0) alive at step t - 1 or t
+#pragma unroll
+        for (int j = 0; j < JA; ++j) {
+            da[j] = __ballot_sync(kFull, !(bma[j] <= ub));
+            db[j] = __ballot_sync(kFull, !(bmb[j] <= ub));
+            const unsigned al = ~(da[j] & db[j]);
+            all_dead = all_dead && al == 0u;
+            if (al) hi = 32 * j + 31 - __clz(al);
+        }
+        const unsigned cond = db[0] & ((da[0] << 1) | 1u);   // retirable leading blocks of window 0
+        if (all_dead || (JA == 1 && cond == kFull)) return 1;
+        const int d = (cond == kFull) ? 32 : (__ffs(~cond) - 1);
+        // windows needed without and with the slide (an alive block needs
+        // CE + 1 blocks after it), capped by the window holding the last column
+        auto need = [&](int sh) {
+            int nd = (hi - sh + CE + 1) / 32 + 1;
+            const int cap_w = (bm - (B0 + sh)) / 32 + 1;
+            nd = nd < cap_w ? nd : cap_w;
+            return nd < 1 ? 1 : nd;
+        };
+        const int n0 = need(0);
+        int nnew = n0, shift = 0;
+        if (d > 0) {
+            const int nd = need(d);
+            if (nd < JA || n0 > JA) {
+                shift = d;
+                nnew = nd;
+            }
+        }
+        if (nnew > J) return 2;   // the live region is wider than J windows
+        if (shift > 0) {
+            // lane l of window j takes block B0 + shift + 32 j + l: from lane
+            // l + shift of window j, or lane l + shift - 32 of window j + 1
+            // (+inf past the active windows); each lane sends the value its
+            // receiver needs.  shift = 32 drops window 0 (every lane takes its
+            // own lane of the next window).
+            B0 += shift;
+            const int src = (lane + shift) & 31;
+            const bool nxt = lane < shift;
+#pragma unroll
+            for (int j = 0; j < JA; ++j) {
+                const bool on = j + 1 < JA;
+                const int jn = j + 1 < J ? j + 1 : j;
+#pragma unroll
+                for (int k = 0; k < K; ++k) {
+                    const float nx = on ? p[jn][k] : INF;
+                    p[j][k] = __shfl_sync(kFull, nxt ? nx : p[j][k], src);
+                }
+                const float n0v = on ? lo0[jn] : INF;
+                const float n1v = on ? lo1[jn] : INF;
+                const float ndv = on ? dg[jn] : INF;
+                lo0[j] = __shfl_sync(kFull, nxt ? n0v : lo0[j], src);
+                lo1[j] = __shfl_sync(kFull, nxt ? n1v : lo1[j], src);
+                dg[j] = __shfl_sync(kFull, nxt ? ndv : dg[j], src);
+                load_q(j);
+            }
+        }
+        // windows switched on start with +inf state; switched-off ones are dropped
+#pragma unroll
+        for (int j = JA; j < J; ++j) {
+            if (j < nnew) {
+                reset(j);
+                load_q(j);
+            }
+        }
+        jact = nnew;
+        // the row pointers move with a slide; near the last row they are capped
+        if (shift > 0 || t + 2 * CE >= B0 + (nre >> 1)) set_zp(t);
+        return 0;
+    };
+
     for (;;) {
         if (t + CE < t_end) {
-#pragma unroll
-            for (int s = 1; s <= CE; ++s) step(t + s, s == CE - 1 ? 1 : (s == CE ? 2 : 0), -1);
-            count_busy(t, t + CE);
-            t += CE;
-            // ---- check ----
-            ub = fminf(ub, __shfl_sync(kFull, BestSoFar::finish(ub_raw), 0));   // one reading for the warp
-            ub_raw = bsf.issue();
-            unsigned da[J], db[J];
-            bool all_dead = true;
-            int hi = -1;   // highest block (relative to B0) alive at step t - 1 or t
-#pragma unroll
-            for (int j = 0; j < J; ++j) {
-                da[j] = kFull;
-                db[j] = kFull;
-                if (j < jact) {
-                    da[j] = __ballot_sync(kFull, !(bma[j] <= ub));
-                    db[j] = __ballot_sync(kFull, !(bmb[j] <= ub));
-                    const unsigned al = ~(da[j] & db[j]);
-                    all_dead = all_dead && al == 0u;
-                    if (al) hi = 32 * j + 31 - __clz(al);
-                }
-            }
-            const unsigned cond = db[0] & ((da[0] << 1) | 1u);   // retirable leading blocks of window 0
-            if (all_dead || (jact == 1 && cond == kFull)) {
-                out.steps = t;
-                break;
-            }
-            const int d = (cond == kFull) ? 32 : (__ffs(~cond) - 1);
-            // windows needed with and without the slide (an alive block needs
-            // CE + 1 blocks after it), capped by the window holding the last column
-            auto need = [&](int shift) {
-                int nd = (hi - shift + CE + 1) / 32 + 1;
-                const int cap_w = (bm - (B0 + shift)) / 32 + 1;
-                nd = nd < cap_w ? nd : cap_w;
-                return nd < 1 ? 1 : nd;
-            };
-            const int n0 = need(0);
-            int nnew = n0;
-            int shift = 0;
-            if (d > 0) {
-                const int nd = need(d);
-                if (nd < jact || n0 > jact) {
-                    shift = d;
-                    nnew = nd;
-                }
-            }
-            // the last active window's end is near an alive block and no
-            // window is left: the live region is wider than J windows
-            if (nnew > J) {
-                out.status = 1;
-                out.steps = t;
-                break;
-            }
-            if (shift > 0) {
-                // lane l of window j takes block B0 + shift + 32 j + l: from lane
-                // l + shift of window j, or lane l + shift - 32 of window j + 1
-                // (+inf past the active windows); each lane sends the value its
-                // receiver needs.  shift = 32 drops window 0 (every lane takes
-                // its own lane of the next window).
-                B0 += shift;
-                const int src = (lane + shift) & 31;
-                const bool nxt = lane < shift;
-#pragma unroll
-                for (int j = 0; j < J; ++j) {
-                    if (j < jact) {
-                        const bool on = j + 1 < jact;
-                        const int jn = j + 1 < J ? j + 1 : j;
-#pragma unroll
-                        for (int k = 0; k < K; ++k) {
-                            const float nx = on ? p[jn][k] : INF;
-                            p[j][k] = __shfl_sync(kFull, nxt ? nx : p[j][k], src);
-                        }
-                        const float n0v = on ? lo0[jn] : INF;
-                        const float n1v = on ? lo1[jn] : INF;
-                        const float ndv = on ? dg[jn] : INF;
-                        lo0[j] = __shfl_sync(kFull, nxt ? n0v : lo0[j], src);
-                        lo1[j] = __shfl_sync(kFull, nxt ? n1v : lo1[j], src);
-                        dg[j] = __shfl_sync(kFull, nxt ? ndv : dg[j], src);
-                        load_q(j);
-                    }
-                }
-            }
-            // switch windows on (state +inf, columns loaded) or off (state reset)
-#pragma unroll
-            for (int j = 0; j < J; ++j) {
-                if (j >= jact && j < nnew) load_q(j);
-                if (j >= nnew && j < jact) reset(j);
-            }
-            jact = nnew;
-            set_zoff(t);
-            continue;
+            int r;
+            if (jact == 1) r = interval(std::integral_constant<int, 1>{});
+            else if (J >= 2 && jact == 2) r = interval(std::integral_constant<int, (J >= 2 ? 2 : 1)>{});
+            else if (J >= 3 && jact == 3) r = interval(std::integral_constant<int, (J >= 3 ? 3 : 1)>{});
+            else r = interval(std::integral_constant<int, J>{});
+            if (r == 0) continue;
+            out.status = r == 2 ? 1 : 0;
+            out.steps = t;
+            break;
         }
-        // the last steps up to t_end (fewer than CE: no check falls before it)
-        const int src = bm - B0;
+        // The last steps up to t_end (at most CE: no check falls before it).
         // Every lane takes every step (the steps shuffle); each captures its
         // own block of the window holding the last column, and the lane of
         // block bm passes it on.  If that block lies beyond the active windows
         // no alive value ever reached it (the switch-on rule): the result is +inf.
-        for (int s = t + 1; s <= t_end; ++s) step(s, 0, (s == t_end && src >= 0) ? src : -1);
-        count_busy(t, t_end);
+        const int src = bm - B0;
+        for (int s = t + 1; s <= t_end; ++s) {
+            float l0[J], l1[J];
+#pragma unroll
+            for (int j = 0; j < J; ++j)
+                if (j < jact) left(j, l0[j], l1[j]);
+#pragma unroll
+            for (int j = 0; j < J; ++j)
+                if (j < jact) cells(j, s, l0[j], l1[j], s == t_end && src >= 0 && j == (src >> 5));
+        }
+        busy += jact * (t_end - t);
         fin = __shfl_sync(kFull, fin, src & 31);
         if (src < 0 || src >= 32 * jact) fin = INF;
         out.dist = (fin <= INF) ? fin : INF;   // NaN (no path through started rows) is +inf
         out.steps = t_end;
         break;
     }
-    int bs = busy;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) bs += __shfl_xor_sync(kFull, bs, o);
-    out.busy = bs;
+    out.busy = 32 * busy;
     return out;
 }
 

@@ -471,7 +471,12 @@ __device__ __forceinline__ DtwOut dtw_warp(const float* __restrict__ rows, float
 constexpr int kCorner = EAPDTW_CORNER;
 static_assert(kCorner >= 2 && kCorner <= 32 && kCorner % 2 == 0, "corner of 2 to 32 rows and columns, even");
 constexpr bool kCornerQInRegs = kCorner <= 16;
-constexpr int kCornerMinLanes = 8;   // run it only when this many lanes are alive
+// Run it only when this many lanes of the tile are alive (a knob for tuning
+// experiments).
+#ifndef EAPDTW_CORNER_MIN_LANES
+#define EAPDTW_CORNER_MIN_LANES 8
+#endif
+constexpr int kCornerMinLanes = EAPDTW_CORNER_MIN_LANES;
 
 template <int COST>
 __device__ __forceinline__ bool corner_dead(const float* x, float a, float cw, float isd, const float* zq, float ub) {

@@ -333,10 +333,10 @@ __device__ __forceinline__ void process_tile(const TileCtx& C, float* s_r, bool 
         DtwOut o;
         if constexpr (EL) {
             static_assert(BAND == 0 && !TIGHT, "the elastic wavefront is unconstrained, without tightening");
-            // the window's z-normalised rows into the warp's buffer (the same
-            // znorm1 values the other wavefront computes row by row)
+            // the window's z-normalised rows, negated, into the warp's buffer
+            // (the same znorm1 values the other wavefront computes row by row)
             const float* xw = s_r + off;
-            for (int i = lane; i < m; i += 32) C.zr[i] = znorm1(xw[i], a_s, cw_s, isd_s);
+            for (int i = lane; i < m; i += 32) C.zr[i] = -znorm1(xw[i], a_s, cw_s, isd_s);
             __syncwarp();
             o = dtw_elastic<kElJ, COST>(C.zr, C.zq, m, m, C.bsf, ub);
             __syncwarp();   // every lane is done with the rows before the next survivor's
