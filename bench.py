@@ -84,10 +84,11 @@ def max_over_ranks(x: float, world: int, device=None) -> float:
     return float(t.item())
 
 
-def job_rate(units_per_rank: float, world: int, ms: float) -> float:
-    """Whole-job throughput: the units all ranks processed over the slowest
-    rank's time per step (each rank runs an independent replica)."""
-    return world * units_per_rank / (ms / 1e3)
+def job_rate(units_total: float, ms: float) -> float:
+    """Whole-job throughput: the units of the whole job (each window of each
+    search is searched by exactly one rank) over the slowest rank's time per
+    step."""
+    return units_total / (ms / 1e3)
 
 
 class ClockSampler:
@@ -189,14 +190,45 @@ def cpu_baseline(n_threads=None):
 # Batched sample: the 1,024-query x 8-reference mix, cut to --batch-queries
 # queries (every query against every reference).
 BATCH_REF_SEED, BATCH_QUERY_SEED = 3, 2
+BATCH_FULL_QUERIES = 1024   # queries of the full mix (each against the 8 references)
+BATCH_REPEATS = 3
 # Serving: a resident random walk of 1e8 points; requests with m log-uniform in
 # [64, 4096], window ratio uniform in [0, 0.5], k in {1, 5}.
 SERVE_N, SERVE_ARRIVAL_SEED, SERVE_QUERY_SEED = 100_000_000, 4, 5
+SERVE_RATES = (0.25, 0.5, 0.9)   # Poisson arrival rates, as fractions of the saturated throughput
+
+
+def batched_mix(nq, seed=BATCH_QUERY_SEED):
+    """Parameters of the batched mix's nq queries in draw order: (m, w, ecg, k)
+    with m log-uniform in [64, 2048], window ratio uniform in [0, 1], random walk
+    or ECG-like by a coin flip, k in {1, 5}."""
+    import math
+    rq = np.random.default_rng(seed)
+    out = []
+    for _ in range(nq):
+        m = int(round(math.exp(rq.uniform(math.log(64), math.log(2048)))))
+        ratio = rq.uniform(0.0, 1.0)
+        w = int(math.ceil(ratio * m))
+        ecg = rq.random() < 0.5
+        k = 1 if rq.random() < 0.5 else 5
+        out.append((m, w, ecg, k, ratio))
+    return out
+
+
+def _stratum(m, ratio):
+    """Stratum of a query of the mix: 4 log-uniform length buckets x 4 window-ratio buckets."""
+    import math
+    lb = min(3, int((math.log(m) - math.log(64)) / ((math.log(2048) - math.log(64)) / 4)))
+    return lb * 4 + min(3, int(ratio * 4))
 
 
 def batched_section(args, dev):
     """Batched search (one graph-captured launch sequence over all items)
-    against the one-query-per-call path on the same items."""
+    against the one-query-per-call path on the same items: a stratified sample
+    of the 1,024-query mix (the first query of each of 16 length x window-ratio
+    strata, each against the 8 references), and the full mix's time estimated
+    from it (each stratum's measured one-call time weighted by its share of the
+    1,024 queries, times the sample's batched/one-call ratio)."""
     import math
     import torch
     from paper_2010_05371_gb300 import api, synth
@@ -204,56 +236,86 @@ def batched_section(args, dev):
     lens = [int(round(math.exp(rr.uniform(math.log(1e5), math.log(1e7))))) for _ in range(8)]
     refs = [torch.from_numpy(synth.random_walk(n, 100 + j).astype(np.float32)).to(dev)
             for j, n in enumerate(lens)]
-    rq = np.random.default_rng(BATCH_QUERY_SEED)
+    mix = batched_mix(BATCH_FULL_QUERIES)
+    counts = {}
+    first = {}
+    for q, (m, w, ecg, k, ratio) in enumerate(mix):
+        st = _stratum(m, ratio)
+        counts[st] = counts.get(st, 0) + 1
+        first.setdefault(st, q)
+    picked = sorted(first.values())[:args.batch_queries]
     queries = []
-    for q in range(args.batch_queries):
-        m = int(round(math.exp(rq.uniform(math.log(64), math.log(2048)))))
-        w = int(math.ceil(rq.uniform(0.0, 1.0) * m))
-        ecg = rq.random() < 0.5
-        k = 1 if rq.random() < 0.5 else 5
+    for q in picked:
+        m, w, ecg, k, ratio = mix[q]
         qn = synth.ecg_query(m, 1000 + q) if ecg else synth.random_walk(m, 1000 + q)
-        queries.append((torch.from_numpy(np.asarray(qn, np.float32)).to(dev), w, k))
+        queries.append((q, torch.from_numpy(np.asarray(qn, np.float32)).to(dev), w, k))
     ctx = api.Context(dev.index or 0)
     ids = [ctx.register(R) for R in refs]
-    items = [(Q, rid, w, k) for (Q, w, k) in queries for rid in ids]
+    items = [(Q, rid, w, k) for (q, Q, w, k) in queries for rid in ids]
+    item_query = [q for (q, Q, w, k) in queries for rid in ids]
     windows = sum(refs[rid].numel() - Q.numel() + 1 for (Q, rid, w, k) in items)
     t0 = time.perf_counter()
     tuned = ctx.autotune(items, sample_windows=1 << 18)   # first-level tile per (length, window) signature
     tune_s = time.perf_counter() - t0
     ctx.search_batch(items, 5)            # warm-up: graph capture, envelope tables
     torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    bi, bd, cnt = ctx.search_batch(items, 5, return_counters=True)
-    torch.cuda.synchronize()
-    tb = time.perf_counter() - t0
+    dev_ms, host_s = [], []
+    cnt = None
+    for _ in range(BATCH_REPEATS):
+        t0 = time.perf_counter()
+        bi, bd, cnt = ctx.search_batch(items, 5, return_counters=True)
+        torch.cuda.synchronize()
+        host_s.append(time.perf_counter() - t0)
+        dev_ms.append(cnt["ns_total"] / 1e6)
+    tb = statistics.median(dev_ms) / 1e3
     big = max(range(len(refs)), key=lambda j: refs[j].numel())
-    api.subseq_search(queries[0][0], refs[big], queries[0][1], 1)   # warm-up of the plain scratch
+    api.subseq_search(queries[0][1], refs[big], queries[0][2], 1)   # warm-up of the plain scratch
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    plain = [api.subseq_search(Q, refs[rid], w, k) for (Q, rid, w, k) in items]
+    plain, plain_ns = [], []
+    for (Q, rid, w, k) in items:
+        pi, pd, pc = api.subseq_search(Q, refs[rid], w, k, return_counters=True)
+        plain.append((pi, pd))
+        plain_ns.append(pc["ns_total"])
     torch.cuda.synchronize()
-    tp = time.perf_counter() - t0
+    tp_host = time.perf_counter() - t0
+    tp = sum(plain_ns) / 1e9
     mism = sum(0 if torch.equal(pd, bd[i, :k]) else 1
                for i, ((Q, rid, w, k), (pi, pd)) in enumerate(zip(items, plain)))
+    # the full mix, estimated per stratum from the sampled query's one-call times
+    per_query_ns = {}
+    for q, ns in zip(item_query, plain_ns):
+        per_query_ns[q] = per_query_ns.get(q, 0) + ns
+    est_plain_s = sum(counts[_stratum(mix[q][0], mix[q][4])] * per_query_ns[q] for q in picked) / 1e9
+    full_windows = sum(sum(n - m + 1 for n in lens) for (m, w, ecg, k, ratio) in mix)
     ctx.close()
     return {
-        "config": (f"batched mix: {args.batch_queries} queries (m log-uniform 64-2048, window ratio "
-                   f"uniform 0-1, random walk or ECG-like, k in {{1,5}}, seed {BATCH_QUERY_SEED}) x 8 "
-                   f"random-walk references (n log-uniform 1e5-1e7, seed {BATCH_REF_SEED}), every "
-                   f"query against every reference; a sample of the 1,024-query mix"),
-        "items": len(items), "windows": windows, "timing": "1 timed run after 1 warm-up, host clock, blocking calls",
+        "config": (f"batched mix: {len(picked)} queries, the first of each length x window-ratio stratum of the "
+                   f"{BATCH_FULL_QUERIES}-query mix (m log-uniform 64-2048, window ratio uniform 0-1, random walk "
+                   f"or ECG-like, k in {{1,5}}, seed {BATCH_QUERY_SEED}) x 8 random-walk references (n log-uniform "
+                   f"1e5-1e7, seed {BATCH_REF_SEED}), every query against every reference"),
+        "items": len(items), "windows": windows,
+        "timing": (f"device time (CUDA events) of the batched launch sequence, median of {BATCH_REPEATS} "
+                   f"after 1 warm-up; the one-call path's device time summed over its calls"),
         "autotune": f"{tuned} signatures tuned in {tune_s:.1f} s before the warm-up (not timed)",
-        "batched_s": round(tb, 4), "plain_s": round(tp, 4),
+        "batched_s": round(tb, 4), "batched_s_repeats": [round(x / 1e3, 4) for x in dev_ms],
+        "batched_host_s": round(statistics.median(host_s), 4),
+        "plain_s": round(tp, 4), "plain_host_s": round(tp_host, 4),
         "batched_windows_per_s": windows / tb, "plain_windows_per_s": windows / tp,
         "batched_queries_per_s": len(items) / tb, "plain_queries_per_s": len(items) / tp,
         "speedup": tp / tb, "executed_cells_per_s": cnt["cells"] / tb,
         "identical_to_plain": f"{len(items) - mism}/{len(items)} items bit-identical distances",
+        "full_mix_estimate": {
+            "queries": BATCH_FULL_QUERIES, "items": BATCH_FULL_QUERIES * len(refs), "windows": full_windows,
+            "plain_s": round(est_plain_s, 2), "batched_s": round(est_plain_s * tb / tp, 2),
+            "basis": "stratum counts of the full mix x each stratum's sampled one-call time; batched = that x the sample's batched/one-call ratio"},
     }
 
 
 def serving_section(args, dev):
-    """Serving loop against a resident 1e8-point reference: all requests at once
-    (saturated), then Poisson arrivals at half the saturated rate."""
+    """Serving loop against a resident 1e8-point reference: every request at
+    once (saturated), the same requests through the one-query-per-call path
+    (plain), and Poisson arrivals at swept fractions of the saturated rate."""
     import math
     import torch
     from paper_2010_05371_gb300 import api, synth
@@ -280,53 +342,63 @@ def serving_section(args, dev):
             pass
 
     def run(reqs, gaps):
-        handles, t_sub = [], []
+        handles = []
         t0 = time.perf_counter()
         for (Q, w, k), g in zip(reqs, gaps):
             if g > 0:
                 time.sleep(g)
             handles.append(ctx.submit(Q, rid, w, k))
-        lat = []
+        lat, res = [], []
         for h, (Q, w, k) in zip(handles, reqs):
             r = None
             while r is None:
                 r = ctx.poll(h, k, timeout_ms=1000)
             lat.append(r[2] / 1e6)
+            res.append((r[0], r[1]))
         wall = time.perf_counter() - t0
         return {"requests": len(reqs), "wall_s": round(wall, 3), "queries_per_s": len(reqs) / wall,
                 "windows_per_s": sum(n - len(Q) + 1 for Q, w, k in reqs) / wall,
                 "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
-                "mean_ms": float(np.mean(lat))}
+                "mean_ms": float(np.mean(lat))}, res
 
     reqs = draw(args.serve_requests, 10_000)
-    sat = run(reqs, [0.0] * len(reqs))
-    lam = 0.5 * sat["queries_per_s"]
-    ra = np.random.default_rng(SERVE_ARRIVAL_SEED)
-    gaps = list(ra.exponential(1.0 / lam, size=args.serve_requests))
-    gaps[0] = 0.0
-    reqs2 = draw(args.serve_requests, 20_000)
-    poi = run(reqs2, gaps)
-    poi["rate_per_s"] = lam
-    # identity: the two shortest requests of the Poisson run, searched alone by the one-query path
-    same = 0
-    short = sorted(range(len(reqs2)), key=lambda i: len(reqs2[i][0]))[:2]
-    for i in short:
-        Q, w, k = reqs2[i]
-        h = ctx.submit(Q, rid, w, k)
-        r = None
-        while r is None:
-            r = ctx.poll(h, k, timeout_ms=1000)
+    sat, sat_res = run(reqs, [0.0] * len(reqs))
+    # the plain path on the same requests: one blocking subseq_search call per
+    # request, in submission order (its latency is queueing plus service)
+    api.subseq_search(torch.from_numpy(reqs[0][0]).to(dev), R, reqs[0][1], reqs[0][2])   # scratch warm-up
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    plain_res, plain_done = [], []
+    for Q, w, k in reqs:
         pi, pd = api.subseq_search(torch.from_numpy(Q).to(dev), R, w, k)
-        same += int(np.array_equal(pd.cpu().numpy(), r[1]))
+        plain_res.append((pi.cpu().numpy(), pd.cpu().numpy()))
+        plain_done.append((time.perf_counter() - t0) * 1e3)
+    plain_wall = time.perf_counter() - t0
+    plain = {"requests": len(reqs), "wall_s": round(plain_wall, 3), "queries_per_s": len(reqs) / plain_wall,
+             "p50_ms": float(np.percentile(plain_done, 50)), "p99_ms": float(np.percentile(plain_done, 99))}
+    same = sum(int(np.array_equal(sd, pd)) for (si, sd), (pi, pd) in zip(sat_res, plain_res))
+    sweep = []
+    ra = np.random.default_rng(SERVE_ARRIVAL_SEED)
+    for j, frac in enumerate(SERVE_RATES):
+        lam = frac * sat["queries_per_s"]
+        gaps = list(ra.exponential(1.0 / lam, size=args.serve_poisson_requests))
+        gaps[0] = 0.0
+        rr = draw(args.serve_poisson_requests, 20_000 + 1000 * j)
+        out, _ = run(rr, gaps)
+        out["rate_per_s"] = lam
+        out["rate_fraction_of_saturated"] = frac
+        sweep.append(out)
     st = ctx.serve_stats()
     ctx.serve_stop()
     ctx.close()
     return {
         "config": (f"serving: resident random walk n={n} (FP32, FP64 chunk sums); requests m log-uniform "
                    f"64-4096, window ratio uniform 0-0.5, k in {{1,5}} (query seed {SERVE_QUERY_SEED}); "
-                   f"{args.serve_active} state slots, 2^22 windows per request per round"),
-        "saturated": sat, "poisson": poi, "rounds": st["rounds"],
-        "identical_to_plain": f"{same}/{len(short)} requests checked",
+                   f"{args.serve_active} state slots, 2^22-window base quantum, cost-ordered rounds"),
+        "saturated": sat, "plain_one_call_per_request": plain,
+        "served_over_plain_queries_per_s": sat["queries_per_s"] / plain["queries_per_s"],
+        "poisson_sweep": sweep, "rounds": st["rounds"],
+        "identical_to_plain": f"{same}/{len(reqs)} requests bit-identical distances",
     }
 
 
@@ -418,8 +490,10 @@ def main():
     ap.add_argument("--queries", default="1,2,3,4",
                     help="query seeds of the step (profiling aid; the benchmark is all four)")
     ap.add_argument("--batch-queries", type=int, default=16,
-                    help="queries of the batched sample (each against 8 references); 0 skips it")
-    ap.add_argument("--serve-requests", type=int, default=24, help="requests per serving run; 0 skips it")
+                    help="strata sampled from the batched mix (one query each, against 8 references); 0 skips it")
+    ap.add_argument("--serve-requests", type=int, default=24,
+                    help="requests of the saturated and plain serving runs; 0 skips serving")
+    ap.add_argument("--serve-poisson-requests", type=int, default=12, help="requests per Poisson rate")
     ap.add_argument("--serve-active", type=int, default=16, help="state slots of the serving loop")
     ap.add_argument("--serve-n", type=int, default=SERVE_N, help="serving reference length")
     ap.add_argument("--no-extensions", action="store_true", help="skip the extensions object")
@@ -461,12 +535,29 @@ def main():
     Qs = [torch.from_numpy(q).to(dev) for q in Qs_np]
     stream = torch.cuda.current_stream(dev)
 
+    from paper_2010_05371_gb300 import shard
+
     def step(Rd, Qd):
+        # one rank: the whole search; N ranks: each rank searches its window
+        # range (with the lQ - 1 halo) and the ranks merge their results
         out = []
         for (w, nolb) in SEARCHES:
             for q, seed in zip(Qd, QUERY_SEEDS):
-                idx, dist_, cnt = api.subseq_search(q, Rd, w, 1, no_lb=nolb, return_counters=True,
-                                                    stream=stream)
+                if world == 1:
+                    idx, dist_, cnt = api.subseq_search(q, Rd, w, 1, no_lb=nolb, return_counters=True,
+                                                        stream=stream)
+                else:
+                    holder = {}
+
+                    def part(Qp, Rp, ww, kk, holder=holder, nolb=nolb):
+                        i_, d_, c_ = api.subseq_search(Qp, Rp, ww, kk, no_lb=nolb, return_counters=True,
+                                                       stream=stream)
+                        holder["c"] = c_
+                        return i_, d_
+
+                    gi, gd = shard.sharded_search(part, q, Rd, w, 1, rank, world, device=dev)
+                    idx, dist_ = torch.from_numpy(gi), torch.from_numpy(gd)
+                    cnt = holder.get("c", {k_: 0 for k_ in api.COUNTER_NAMES})
                 out.append((seed, w, nolb, idx, dist_, cnt))
         return out
 
@@ -483,6 +574,10 @@ def main():
     step_ms = []
     results = None
     main_ns = wider_ns = cells = launches = 0
+    # per kind of search (nolb: the unconstrained searches without lower
+    # bounds, whose first level is the dominant kernel; cascade: w = 103 with
+    # the lower bounds): kernel ns, executed cells, searches
+    per_kind = {True: [0, 0, 0], False: [0, 0, 0]}
     with ClockSampler(gpu_id) as clocks:
         barrier()
         torch.cuda.synchronize()
@@ -500,6 +595,10 @@ def main():
                 wider_ns += c["ns_wider"]
                 cells += c["cells"]
                 launches += c["launches"]
+                pk = per_kind[bool(r[2])]
+                pk[0] += c["ns_main"] + c["ns_wider"]
+                pk[1] += c["cells"]
+                pk[2] += 1
         torch.cuda.synchronize()
         barrier()
         t_wall = time.perf_counter() - t_wall0
@@ -507,7 +606,8 @@ def main():
         peak_rates = {m: api.cell_peak(m, PEAK_STEPS)[0] for m in PEAK_MODES}
         peak_rates["best"] = max(peak_rates.values())
     ms = max_over_ranks(sum(step_ms) / len(step_ms), world, dev)
-    value = job_rate(len(SEARCHES) * len(QUERY_SEEDS) * nw, world, ms)
+    # every window of every search is processed once, by one rank
+    value = job_rate(len(SEARCHES) * len(QUERY_SEEDS) * nw, ms)
 
     # ---- end to end: the host-buffer entry point (subseq_search_host) on
     # pinned host arrays; every call copies its R and Q in and its result out ----
@@ -519,13 +619,21 @@ def main():
         flush.zero_()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        host = [api.subseq_search_host(qh, R_pin, w, 1, no_lb=nolb)
-                for (w, nolb) in SEARCHES for qh in Q_pin]
+        if world == 1:
+            host = [api.subseq_search_host(qh, R_pin, w, 1, no_lb=nolb)
+                    for (w, nolb) in SEARCHES for qh in Q_pin]
+        else:   # each rank copies in its slice only
+            host = [shard.sharded_search(lambda Qp, Rp, ww, kk, nolb=nolb: api.subseq_search_host(Qp, Rp, ww, kk, no_lb=nolb),
+                                         qh, R_pin, w, 1, rank, world, device=dev)
+                    for (w, nolb) in SEARCHES for qh in Q_pin]
         if it > 0:  # first iteration warms the host path's scratch
             e2e_ms.append((time.perf_counter() - t0) * 1e3)
     e2e_step_ms = max_over_ranks(statistics.mean(e2e_ms), world, dev)
-    e2e = {"value": job_rate(len(SEARCHES) * len(QUERY_SEEDS) * nw, world, e2e_step_ms),
-           "unit": "windows/s", "h2d_bytes_per_step": len(host) * (4 * n + 4 * M),
+    e2e = {"value": job_rate(len(SEARCHES) * len(QUERY_SEEDS) * nw, e2e_step_ms),
+           "unit": "windows/s",
+           "h2d_bytes_per_step": len(host) * (4 * (shard.slice_bounds(*shard.window_ranges(nw, world)[rank], M)[1]
+                                                   - shard.slice_bounds(*shard.window_ranges(nw, world)[rank], M)[0])
+                                              + 4 * M),
            "d2h_bytes_per_step": 16 * len(host), "ms_per_step": e2e_step_ms,
            "api": "subseq_search_host, one call per search, pinned host buffers"}
 
@@ -533,30 +641,44 @@ def main():
     nsearch = args.steps * len(results)
     clk = clocks.summary()
     golden = load_golden(n)
-    alg_cells = None
-    if golden:
-        alg_cells = args.steps * sum(golden[(r[0], r[1], not r[2])]["audit_counters"]["cells"]
-                                     for r in results)
-    # every search_kernel launch of the search except the seed pass: the first
-    # level (all windows) and the re-runs of overflowed windows with wider tiles
-    kern_s = (main_ns + wider_ns) / 1e9
-    roof = None
-    if kern_s > 0:
-        used_cells = alg_cells if alg_cells is not None else cells
-        achieved = used_cells / kern_s / 1e12
-        executed = cells / kern_s / 1e12
-        peak = peak_rates["best"] / 1e12
-        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tcells/s",
-                "frac": achieved / peak, "traffic": TRAFFIC_BYTES_PER_SEARCH,
-                "kernel": "search_kernel (LB cascade + EAPrunedDTW wavefront), all levels of a search",
-                "kernel_ms_per_search": (main_ns + wider_ns) / 1e6 / nsearch,
+
+    def alg_of(kind):
+        if not golden:
+            return None
+        return args.steps * sum(golden[(r[0], r[1], not r[2])]["audit_counters"]["cells"]
+                                for r in results if bool(r[2]) == kind)
+
+    peak = peak_rates["best"] / 1e12
+
+    def roof_of(kind, kernel, traffic):
+        ns, ex, ns_count = per_kind[kind]
+        if ns <= 0:
+            return None
+        alg = alg_of(kind)
+        used = alg if alg is not None else ex
+        achieved = used / (ns / 1e9) / 1e12
+        executed = ex / (ns / 1e9) / 1e12
+        return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tcells/s",
+                "frac": achieved / peak, "traffic": traffic, "kernel": kernel,
+                "kernel_ms_per_search": ns / 1e6 / ns_count,
                 "work": ("algorithmic cells (oracle audit-mode EAPrunedDTW count at ub = NN distance)"
-                         if alg_cells is not None else "executed cells (no oracle count available)"),
+                         if alg is not None else "executed cells (no oracle count available)"),
                 "executed_cells_achieved": executed, "executed_cells_frac": executed / peak,
-                "executed_over_algorithmic": (cells / alg_cells) if alg_cells else None,
+                "executed_over_algorithmic": (ex / alg) if alg else None,
                 "peak_basis": ("measured: eapdtw_cell_peak, the DP cell alone on every SM (CUDA events, "
                                "fastest of 3 launches), the fastest of its modes"),
                 "peak_modes_tcells": {str(k): v / 1e12 for k, v in peak_rates.items() if k != "best"}}
+
+    # the dominant kernel: the unconstrained searches' levels (the elastic
+    # first level and its re-runs), timed with CUDA events inside the library
+    roof = None if world > 1 else roof_of(True, "search_elastic_kernel (EAPrunedDTW elastic wavefront, unconstrained first level) "
+                         "with its wider re-run levels", TRAFFIC_BYTES_PER_SEARCH)
+    # the cascade searches (LB_Kim / LB_Keogh terms and banded DP cells; only
+    # the DP cells are counted as work here)
+    roof_cascade = None if world > 1 else roof_of(False, "search_kernel (LB cascade + banded EAPrunedDTW wavefront), all levels", None)
+    alg_cells = None
+    if golden:
+        alg_cells = (alg_of(True) or 0) + (alg_of(False) or 0)
 
     # parity of this run's answers against the oracle's full-size results: the
     # distance within the tolerance of the oracle's; the index the oracle's, or
@@ -597,17 +719,19 @@ def main():
         line = {
             "metric": METRIC, "value": value, "unit": "windows/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "higher_is_better": True, "scaling": "strong", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
             "config": {"workload": workload_desc(n), "n": n, "m": M, "queries": len(QUERY_SEEDS),
                        "w": [w for w, _ in SEARCHES], "k": 1,
                        "l2": "flushed between steps (256 MiB write outside the timed events)",
-                       "parallelism": f"{world} independent replica(s)"},
+                       "parallelism": (f"window-range sharding over {world} ranks, merged by all-reduce MIN"
+                                       if world > 1 else "1 GPU")},
             "dtw_cells_per_s": world * cells / args.steps / (ms / 1e3),
             "algorithmic_cells_per_s": (world * alg_cells / args.steps / (ms / 1e3)) if alg_cells else None,
             "queries_per_s": world * len(results) / (ms / 1e3),
             "search_ms": {k: round(statistics.mean(v), 3) for k, v in per_mode.items()},
             "roofline": roof,
+            "roofline_cascade": roof_cascade,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": launches,

@@ -292,7 +292,9 @@ int32_t eapdtw_ctx_info(eapdtw_ctx* ctx, int64_t* out, int32_t nout);
  * (DEVICE arrays of n*kstride), ascending by (distance, index) as in
  * subseq_search; slots k..kstride-1 hold (-1, +inf).  Items that share the
  * same (Q pointer, lQ, w) share one query preparation.  counters: optional
- * HOST int64[EAPDTW_NCOUNTERS] with the summed counters 0..9 of the batch.
+ * HOST int64[EAPDTW_NCOUNTERS] with the summed counters 0..9 of the batch and, at
+ * EAPDTW_CNT_NS_TOTAL, the device time of its launch sequence (CUDA events on
+ * `stream`; items re-run alone after a full re-run list are not included).
  * Blocking.  The launch sequence is captured into a CUDA graph on the first
  * call (and again after the context's arena grows), so the call must not be
  * made while `stream` is being captured.  kstride <= EAPDTW_MAX_K. */

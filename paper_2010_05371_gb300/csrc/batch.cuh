@@ -97,6 +97,8 @@ struct BatchDev {
     int* nbest;                  // [cap_states]
     long long* best;             // [cap_states * kBatchSeedBest]
     int* flags;                  // [cap_states] bit 0: an overflow entry was lost
+    unsigned long long* cost;    // [cap_states] SM clock cycles the warps spent on the state's
+                                 // work units in this launch sequence (the serving loop's cost estimate)
     float* seed_ed;              // [cap_samples]
     int* seed_idx;               // [cap_samples]
     int64_t* res_idx;            // [cap_items * kstride]
@@ -238,7 +240,9 @@ batch_kernel(const BatchLaunch L) {
         C.cbw = nullptr;
         C.lost = seed ? nullptr : L.D.flags + it.state;   // a seed is only a hint: nothing is lost
         C.dbg = nullptr;
+        const long long c0 = clock64();
         process_tile<K, BAND, JW <= 1, JW, false, 2>(C, nullptr, list, i0, nl, count);
+        if (lane == 0) atomicAdd(L.D.cost + it.state, static_cast<unsigned long long>(clock64() - c0));
     }
     __syncthreads();
     if (threadIdx.x < 10 && s_cnt[threadIdx.x]) atomicAdd(L.counters + threadIdx.x, s_cnt[threadIdx.x]);

@@ -97,6 +97,7 @@ BatchDev dev_view(Arena& a) {
     D.nbest = a.nbest;
     D.best = a.best;
     D.flags = a.flags;
+    D.cost = a.cost;
     D.seed_ed = a.seed_ed;
     D.seed_idx = a.seed_idx;
     D.res_idx = a.res_idx;
@@ -338,7 +339,7 @@ void plan_item(const eapdtw_ctx* c, const RefEntry& r, int64_t n_used, int m, in
 void arena_free(eapdtw_ctx* c, Arena& a) {
     drop_graph(a);
     dfree(a.tables); dfree(a.qarena); dfree(a.qbad); dfree(a.slots); dfree(a.ub_seed);
-    dfree(a.nbest); dfree(a.best); dfree(a.flags); dfree(a.seed_ed); dfree(a.seed_idx);
+    dfree(a.nbest); dfree(a.best); dfree(a.flags); dfree(a.cost); dfree(a.seed_ed); dfree(a.seed_idx);
     dfree(a.res_idx); dfree(a.res_dist); dfree(a.rr); dfree(a.small);
     if (a.htables) cudaFreeHost(a.htables);
     if (a.hbuf) cudaFreeHost(a.hbuf);
@@ -371,7 +372,8 @@ int32_t arena_reserve(eapdtw_ctx* c, Arena& a, int items, int qslots, int states
     const bool ok = dalloc(a.tables, lay.total, bytes) && dalloc(a.qarena, cq, bytes) && dalloc(a.qbad, cs, bytes) &&
                     dalloc(a.slots, ct * kBatchSlots, bytes) && dalloc(a.ub_seed, ct, bytes) &&
                     dalloc(a.nbest, ct, bytes) && dalloc(a.best, ct * kBatchSeedBest, bytes) &&
-                    dalloc(a.flags, ct, bytes) && dalloc(a.seed_ed, cm, bytes) && dalloc(a.seed_idx, cm, bytes) &&
+                    dalloc(a.flags, ct, bytes) && dalloc(a.cost, ct, bytes) && dalloc(a.seed_ed, cm, bytes) &&
+                    dalloc(a.seed_idx, cm, bytes) &&
                     dalloc(a.res_idx, rows, bytes) && dalloc(a.res_dist, rows, bytes) &&
                     dalloc(a.rr, 3 * kRerunBuffers * cr, bytes) && dalloc(a.small, 1024, bytes);
     a.bytes = bytes;
@@ -380,7 +382,7 @@ int32_t arena_reserve(eapdtw_ctx* c, Arena& a, int items, int qslots, int states
         arena_free(c, a);
         return EAPDTW_ERR_OUT_OF_MEMORY;
     }
-    const size_t hb = Arena::al8(sizeof(int) * (ct + cs)) + sizeof(unsigned long long) * 2 * kNumCounters;
+    const size_t hb = Arena::al8(sizeof(int) * (ct + cs)) + sizeof(unsigned long long) * (2 * kNumCounters + ct);
     if (cudaHostAlloc(reinterpret_cast<void**>(&a.htables), lay.total, cudaHostAllocDefault) != cudaSuccess ||
         cudaHostAlloc(reinterpret_cast<void**>(&a.hbuf), hb, cudaHostAllocDefault) != cudaSuccess ||
         cudaHostAlloc(reinterpret_cast<void**>(&a.hres_idx), sizeof(int64_t) * rows, cudaHostAllocDefault) !=
@@ -472,6 +474,7 @@ int32_t arena_run(Arena& a, std::vector<PlannedItem>& items, const std::vector<Q
     if (nslots) CKC(cudaMemcpyAsync(a.hqbad(), a.qbad, sizeof(int) * nslots, cudaMemcpyDeviceToHost, st));
     CKC(cudaMemcpyAsync(a.hcounters(), a.counters(), sizeof(unsigned long long) * 2 * kNumCounters,
                         cudaMemcpyDeviceToHost, st));
+    CKC(cudaMemcpyAsync(a.hcost(), a.cost, sizeof(unsigned long long) * a.cap_states, cudaMemcpyDeviceToHost, st));
     return EAPDTW_OK;
 }
 
@@ -792,7 +795,12 @@ int32_t eapdtw_search_batch(eapdtw_ctx* c, const eapdtw_item* items, int32_t n, 
     std::lock_guard<std::mutex> lk(c->mu);
     DeviceGuard g(c->device);
     if (!g.ok) return EAPDTW_ERR_CUDA;
-    return run_batch(c, items, n, kstride, out_idx, out_dist, counters, stream, nullptr, nullptr);
+    if (!counters) return run_batch(c, items, n, kstride, out_idx, out_dist, nullptr, stream, nullptr, nullptr);
+    // with counters, the launch sequence is timed with CUDA events on the call's stream
+    float ms = 0.0f;
+    const int32_t rc = run_batch(c, items, n, kstride, out_idx, out_dist, counters, stream, nullptr, &ms);
+    if (rc == EAPDTW_OK) counters[EAPDTW_CNT_NS_TOTAL] = static_cast<int64_t>(static_cast<double>(ms) * 1.0e6);
+    return rc;
 }
 
 int32_t eapdtw_autotune(eapdtw_ctx* c, const eapdtw_item* items, int32_t n, int64_t sample_windows, void* stream,

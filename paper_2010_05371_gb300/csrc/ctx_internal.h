@@ -59,13 +59,14 @@ struct Arena {
     int* nbest = nullptr;
     long long* best = nullptr;
     int* flags = nullptr;
+    unsigned long long* cost = nullptr;  // [cap_states] GPU cycles per state of the last launch sequence
     float* seed_ed = nullptr;
     int* seed_idx = nullptr;
     int64_t* res_idx = nullptr;
     double* res_dist = nullptr;
     long long* rr = nullptr;             // [kRerunBuffers][3][rr_cap]
     unsigned char* small = nullptr;      // rr counts [16] | work [32] | counters [16] | seed counters [16]
-    unsigned char* hbuf = nullptr;       // pinned: flags [cap_states] | query flags [cap_slots] | counters
+    unsigned char* hbuf = nullptr;       // pinned: flags [cap_states] | query flags [cap_slots] | counters | cost [cap_states]
     int64_t* hres_idx = nullptr;         // pinned result rows (serving)
     double* hres_dist = nullptr;
     cudaStream_t cap_stream = nullptr;   // stream the launch sequence is captured on
@@ -82,6 +83,7 @@ struct Arena {
     unsigned long long* hcounters() {
         return reinterpret_cast<unsigned long long*>(hbuf + al8(sizeof(int) * (static_cast<int64_t>(cap_states) + cap_slots)));
     }
+    unsigned long long* hcost() { return hcounters() + 2 * kNumCounters; }
     static int64_t al8(int64_t x) { return (x + 7) / 8 * 8; }
 };
 

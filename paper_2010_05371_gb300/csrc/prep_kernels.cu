@@ -448,6 +448,7 @@ __global__ void batch_init_kernel(BatchDev D, int cap_items, unsigned long long*
             D.nbest[it.state] = 0;
         }
         D.flags[it.state] = 0;
+        D.cost[it.state] = 0;
     }
     for (int64_t j = tid; j < *D.nslots; j += stride) D.qbad[j] = 0;
     if (tid < ncounters) counters[tid] = 0;

@@ -1,10 +1,19 @@
 // Serving loop of a context (declared in include/eapdtw.h): requests arrive
 // from any host thread; a server thread admits them into resident state slots
 // and runs rounds of the batched launch sequence (batch.cuh).  Each round
-// takes the next chunk of windows of every admitted request, so requests that
-// arrive while others are on the GPU join at the next round and their work
-// overlaps with the others'; a request's k-best list, seed bound and prepared
-// query stay on the device from its first round to its last.
+// takes the next windows of every admitted request, so requests that arrive
+// while others are on the GPU join at the next round and their work overlaps
+// with the others'; a request's k-best list, seed bound and prepared query
+// stay on the device from its first round to its last.
+//
+// How many windows a request gets in a round: the batch kernel measures, per
+// request, the SM cycles its warps spent, so each request has an estimate of
+// its cost per window after its first round (which takes chunk windows).  A
+// round's budget is what chunk windows of every admitted request would cost;
+// it goes to the requests in order of their estimated remaining cost
+// (shortest remaining first), each at least a floor of windows so that none
+// starves, and at most kMaxChunks chunks.  So a cheap request is not held for
+// the whole mix: it finishes in a few rounds while the expensive ones go on.
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
@@ -40,6 +49,7 @@ struct Request {
     bool started = false;
     bool cancel = false;
     bool lost = false;
+    double cpw = -1.0;      // estimated SM cycles per window (< 0: not measured yet)
     int32_t status = EAPDTW_PENDING;
     Clock::time_point t_submit, t_admit, t_done;
     int64_t idx[EAPDTW_MAX_K];
@@ -103,9 +113,53 @@ int32_t finish_lost(Server* S, Request* r) {
 
 }  // namespace
 
+// Windows each admitted request gets in a round (see the file's header).
+constexpr int64_t kMaxChunks = 8;
+std::vector<int64_t> allocate_windows(const std::vector<Request*>& act, int64_t chunk) {
+    std::vector<int64_t> nwin(act.size(), 0);
+    const int64_t floor_w = std::max<int64_t>(32, chunk / 16);
+    double budget = 0.0;
+    std::vector<size_t> known;
+    for (size_t i = 0; i < act.size(); ++i) {
+        const Request* r = act[i];
+        const int64_t rem = r->nw - r->next;
+        if (r->cpw < 0.0) {
+            nwin[i] = std::min<int64_t>(chunk, rem);   // first round: measure
+        } else {
+            budget += static_cast<double>(std::min<int64_t>(chunk, rem)) * r->cpw;
+            known.push_back(i);
+        }
+    }
+    std::sort(known.begin(), known.end(), [&](size_t a, size_t b) {
+        const double ca = static_cast<double>(act[a]->nw - act[a]->next) * act[a]->cpw;
+        const double cb = static_cast<double>(act[b]->nw - act[b]->next) * act[b]->cpw;
+        return ca < cb || (ca == cb && act[a]->id < act[b]->id);
+    });
+    // every known request first gets its floor, then the rest of the budget in order
+    for (size_t i : known) {
+        const Request* r = act[i];
+        nwin[i] = std::min<int64_t>(floor_w, r->nw - r->next);
+        budget -= static_cast<double>(nwin[i]) * r->cpw;
+    }
+    for (size_t i : known) {
+        const Request* r = act[i];
+        const int64_t rem = r->nw - r->next - nwin[i];
+        if (rem <= 0 || budget <= 0.0) continue;
+        const double afford = r->cpw > 0.0 ? budget / r->cpw : static_cast<double>(rem);
+        int64_t extra = std::min<int64_t>(rem, static_cast<int64_t>(std::min(afford, 1e18)));
+        extra = std::min<int64_t>(extra, kMaxChunks * chunk - nwin[i]);
+        if (extra < rem) extra = extra / 32 * 32;   // whole tiles, or the whole tail
+        if (extra <= 0) continue;
+        nwin[i] += extra;
+        budget -= static_cast<double>(extra) * r->cpw;
+    }
+    return nwin;
+}
+
 // One round over the admitted requests `act` (the server thread; S->mu not held).
 int32_t Server::round(std::vector<Request*>& act) {
     std::vector<PlannedItem> P(act.size());
+    const std::vector<int64_t> alloc = allocate_windows(act, chunk);
     std::vector<QuerySlot> qs;
     {
         std::lock_guard<std::mutex> lk(c->mu);
@@ -117,7 +171,7 @@ int32_t Server::round(std::vector<Request*>& act) {
             b.state = r->state;
             b.fresh = r->started ? 0 : 1;
             b.win0 = r->next;
-            b.nwin = std::min<int64_t>(chunk, r->nw - r->next);
+            b.nwin = alloc[i];
             if (r->started) b.seed_ns = 0;   // seeds run in the first round only
             P[i].tiles = (b.nwin + 31) / 32;
             const int64_t off = static_cast<int64_t>(r->state) * 5 * query_pad(EAPDTW_MAX_QUERY);
@@ -172,6 +226,12 @@ int32_t Server::round(std::vector<Request*>& act) {
             r->started = true;
             r->lost |= (hf[r->state] & 1) != 0;
             windows += P[i].b.nwin;
+            // cost per window: this round's measurement, smoothed over rounds
+            // (the first round also prepared the query and ran the seeds)
+            if (P[i].b.nwin > 0) {
+                const double c = static_cast<double>(A.hcost()[r->state]) / static_cast<double>(P[i].b.nwin);
+                r->cpw = r->cpw < 0.0 ? c : 0.5 * (r->cpw + c);
+            }
             if (r->status == EAPDTW_PENDING) r->next += P[i].b.nwin;
             if (r->next >= r->nw) {
                 std::memcpy(r->idx, A.hres_idx + i * EAPDTW_MAX_K, sizeof(int64_t) * r->k);
@@ -358,7 +418,9 @@ int32_t eapdtw_serve_start(eapdtw_ctx* c, int32_t max_active, int64_t chunk_wind
     }
     c->used += dq_bytes;
     // the arena for max_active items in max_active states, each round's
-    // re-run lists sized for every admitted request's chunk
+    // re-run lists sized for every admitted request's chunk (a round may give
+    // one request up to kMaxChunks chunks; a list that fills up marks its
+    // items for a search alone, so the results never depend on the sizing)
     const int64_t qf = static_cast<int64_t>(max_active) * 5 * query_pad(EAPDTW_MAX_QUERY);
     const int64_t samples = static_cast<int64_t>(max_active) * kBatchSeedSamples;
     const int64_t rr = static_cast<int64_t>(max_active) * (S->chunk + kBatchSeedBest);
