@@ -52,9 +52,9 @@ GOLDEN = os.path.join(ROOT, "tests", "golden", "bench_large_oracle.json")
 PEAK_STEPS = 1 << 18
 PEAK_MODES = (0, 1, 2, 3)
 # DRAM bytes (read + write) of the dominant search kernel per search: the ncu
-# capture of the first-level launch at n = 1e7, scaled to the workload's 2e7
-# windows; None until a capture of the current kernel exists.
-TRAFFIC_BYTES_PER_SEARCH = None
+# capture of the elastic first-level launch at n = 1e7 (208.3 MB for 9,998,977
+# windows), scaled to the workload's 19,998,977 windows.
+TRAFFIC_BYTES_PER_SEARCH = 4.166e8
 # CPU baseline sample (oracle): windows of the cascade (w=103) and nolb (w=1024) searches
 CPU_SAMPLE = {"cascade_windows": 2_000_000, "nolb_windows": 200_000, "query_seed": 1}
 
