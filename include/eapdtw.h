@@ -311,14 +311,29 @@ int32_t eapdtw_set_first_tile(eapdtw_ctx* ctx, int32_t log2_m, int32_t ratio_ten
 /* eapdtw_get_first_tile - the table entry (0 = none, the built-in rule). */
 int32_t eapdtw_get_first_tile(eapdtw_ctx* ctx, int32_t log2_m, int32_t ratio_tenths, int32_t band, int32_t* tile);
 
-/* eapdtw_autotune - the autotuner of the first level's DP cells per lane.
- * For every signature (see eapdtw_set_first_tile) of the n HOST items that
- * has no table entry yet, it times the batched search of one representative
- * item (the one with the longest reference) over a prefix of its reference
- * holding about sample_windows windows, with the built-in choice, twice it
- * and half it (two runs each, the faster counts, device time of the launch
- * sequence), and enters the fastest.  *n_tuned (optional) receives the number
- * of signatures entered.  Blocking; results of later searches are unchanged. */
+/* eapdtw_set_tuning - the autotuner's whole choice for a signature (see
+ * eapdtw_set_first_tile): the first level's DP cells per lane (4, 8, 16, 32; 0
+ * = the built-in rule) and check_double (1: the warp wavefront checks its
+ * borders and the best-so-far bound at twice its built-in interval of 8
+ * steps, 16 for the one-window unconstrained levels; 0: the built-in
+ * interval).  Both 0 removes the entry.  Any choice gives the same results. */
+int32_t eapdtw_set_tuning(eapdtw_ctx* ctx, int32_t log2_m, int32_t ratio_tenths, int32_t band, int32_t tile,
+                          int32_t check_double);
+
+/* eapdtw_get_tuning - the table entry (0, 0 = none). */
+int32_t eapdtw_get_tuning(eapdtw_ctx* ctx, int32_t log2_m, int32_t ratio_tenths, int32_t band, int32_t* tile,
+                          int32_t* check_double);
+
+/* eapdtw_autotune - the autotuner of the first level's DP cells per lane and
+ * of the wavefront's check (poll) interval.  For every signature (see
+ * eapdtw_set_first_tile) of the n HOST items that has no table entry yet, it
+ * times the batched search of one representative item (the one with the
+ * longest reference) over a prefix of its reference holding about
+ * sample_windows windows, with the built-in K, twice it and half it, each at
+ * the built-in check interval and at twice it (two runs each, the faster
+ * counts, device time of the launch sequence), and enters the fastest pair.
+ * *n_tuned (optional) receives the number of signatures entered.  Blocking;
+ * results of later searches are unchanged. */
 int32_t eapdtw_autotune(eapdtw_ctx* ctx, const eapdtw_item* items, int32_t n, int64_t sample_windows,
                         void* stream, int32_t* n_tuned);
 

@@ -121,6 +121,10 @@ def lib():
         L.eapdtw_set_first_tile.argtypes = [vp, i32, i32, i32, i32]
         L.eapdtw_get_first_tile.restype = i32
         L.eapdtw_get_first_tile.argtypes = [vp, i32, i32, i32, pi32]
+        L.eapdtw_set_tuning.restype = i32
+        L.eapdtw_set_tuning.argtypes = [vp, i32, i32, i32, i32, i32]
+        L.eapdtw_get_tuning.restype = i32
+        L.eapdtw_get_tuning.argtypes = [vp, i32, i32, i32, pi32, pi32]
         L.eapdtw_autotune.restype = i32
         L.eapdtw_autotune.argtypes = [vp, C.POINTER(Item), i32, i64, vp, pi32]
         pi64 = C.POINTER(i64)
@@ -424,7 +428,7 @@ class Context:
         del keep
         _check(rc, "eapdtw_search_batch")
         if return_counters:
-            return idx, dist, dict(zip(COUNTER_NAMES[:10], (int(c) for c in cnt[:10])))
+            return idx, dist, dict(zip(COUNTER_NAMES, (int(c) for c in cnt)))   # 0..9 summed, ns_total timed
         return idx, dist
 
     def autotune(self, items, sample_windows: int = 1 << 18, stream=None) -> int:
@@ -486,22 +490,33 @@ class Context:
         return dict(zip(SERVE_STAT_NAMES, (int(v) for v in out)))
 
     # ---- autotuner table: persisted per GPU model ---------------------------
+    def set_tuning(self, log2_m: int, ratio_tenths: int, band: int, tile: int, check_double: int):
+        """The autotuner's choice for a signature: first-level tile and check interval (0/1)."""
+        _check(lib().eapdtw_set_tuning(self._h, log2_m, ratio_tenths, band, tile, check_double),
+               "eapdtw_set_tuning")
+
+    def get_tuning(self, log2_m: int, ratio_tenths: int, band: int):
+        t, c = C.c_int32(), C.c_int32()
+        _check(lib().eapdtw_get_tuning(self._h, log2_m, ratio_tenths, band, C.byref(t), C.byref(c)),
+               "eapdtw_get_tuning")
+        return t.value, c.value
+
     def tuning_table(self) -> dict:
-        """The first-level tile choices in effect: {(log2_m, ratio_tenths, band): tile}."""
+        """The choices in effect: {(log2_m, ratio_tenths, band): (tile, check_double)}."""
         out = {}
         for lg in range(13):
             for tenth in range(11):
                 for band in (0, 1):
-                    t = self.get_first_tile(lg, tenth, band)
-                    if t:
-                        out[(lg, tenth, band)] = t
+                    t, c = self.get_tuning(lg, tenth, band)
+                    if t or c:
+                        out[(lg, tenth, band)] = (t, c)
         return out
 
     def save_tuning(self, path: str):
         """Write the tuning table to a JSON file, keyed by this device's name."""
         import json
         import torch
-        entries = [[lg, tenth, band, tile] for (lg, tenth, band), tile in sorted(self.tuning_table().items())]
+        entries = [[lg, tenth, band, tile, chk] for (lg, tenth, band), (tile, chk) in sorted(self.tuning_table().items())]
         with open(path, "w") as f:
             json.dump({"device": torch.cuda.get_device_name(self.device), "entries": entries}, f, indent=1)
 
@@ -514,6 +529,7 @@ class Context:
             data = json.load(f)
         if data.get("device") != torch.cuda.get_device_name(self.device):
             return 0
-        for lg, tenth, band, tile in data.get("entries", []):
-            self.set_first_tile(lg, tenth, band, tile)
+        for e in data.get("entries", []):
+            lg, tenth, band, tile = e[:4]
+            self.set_tuning(lg, tenth, band, tile, e[4] if len(e) > 4 else 0)
         return len(data.get("entries", []))

@@ -57,6 +57,7 @@ struct BatchItem {
     int fresh;           // 1: the state starts from empty in this launch sequence
     int m, w, k, use_lb;
     int seed_ns;         // sampled windows (0: no seed)
+    int check2;          // 1: the wavefront checks at twice its built-in interval (autotuner)
     int level0;          // first level
     int next_level[kBatchLevels];  // level that re-runs windows overflowing level L (-1: none)
     int next_band[kBatchLevels];   // its band mode
@@ -238,6 +239,8 @@ batch_kernel(const BatchLaunch L) {
         C.ovf_cap = rl >= 0 ? L.rr_cap : 0;
         C.tag = static_cast<long long>(item) << 32;
         C.cbw = nullptr;
+        C.zr = nullptr;
+        C.check2 = it.check2;
         C.lost = seed ? nullptr : L.D.flags + it.state;   // a seed is only a hint: nothing is lost
         C.dbg = nullptr;
         const long long c0 = clock64();

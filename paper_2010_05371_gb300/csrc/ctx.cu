@@ -292,10 +292,14 @@ int first_level(const eapdtw_ctx* c, int m, int w) {
             if (32 * k >= m) { K = k; break; }
     }
     auto it = c->tuned.find(signature(m, w));
-    if (it != c->tuned.end()) K = it->second;
+    if (it != c->tuned.end() && it->second.first) K = it->second.first;
     int level = 0;
     while ((4 << level) < K) ++level;
     return level;
+}
+int check_choice(const eapdtw_ctx* c, int m, int w) {
+    auto it = c->tuned.find(signature(m, w));
+    return it != c->tuned.end() ? it->second.second : 0;
 }
 
 int band_mode(int level, int w, bool unconstrained) {
@@ -318,6 +322,7 @@ void plan_item(const eapdtw_ctx* c, const RefEntry& r, int64_t n_used, int m, in
     b.use_lb = no_lb ? 0 : 1;
     b.seed_ns = b.nw >= 2048 ? static_cast<int>(std::min<int64_t>(b.nw, kBatchSeedSamples)) : 0;
     b.level0 = first_level(c, m, w);
+    b.check2 = check_choice(c, m, w);
     const int last = batch_last_level(m);
     for (int lv = 0; lv < kBatchLevels; ++lv) {
         const int nx = lv < 3 ? lv + 1 : (lv == 3 && last > 3 ? last : -1);
@@ -775,8 +780,10 @@ int32_t eapdtw_set_first_tile(eapdtw_ctx* c, int32_t log2_m, int32_t ratio_tenth
     if (tile != 0 && tile != 4 && tile != 8 && tile != 16 && tile != 32) return EAPDTW_ERR_INVALID_ARG;
     std::lock_guard<std::mutex> lk(c->mu);
     const auto key = std::make_tuple(static_cast<int>(log2_m), static_cast<int>(ratio_tenths), static_cast<int>(band));
-    if (tile == 0) c->tuned.erase(key);
-    else c->tuned[key] = tile;
+    auto f = c->tuned.find(key);
+    const int chk = f == c->tuned.end() ? 0 : f->second.second;
+    if (tile == 0 && chk == 0) c->tuned.erase(key);
+    else c->tuned[key] = std::make_pair(static_cast<int>(tile), chk);
     return EAPDTW_OK;
 }
 
@@ -784,7 +791,30 @@ int32_t eapdtw_get_first_tile(eapdtw_ctx* c, int32_t log2_m, int32_t ratio_tenth
     if (!c || !tile) return EAPDTW_ERR_INVALID_ARG;
     std::lock_guard<std::mutex> lk(c->mu);
     auto f = c->tuned.find(std::make_tuple(static_cast<int>(log2_m), static_cast<int>(ratio_tenths), static_cast<int>(band)));
-    *tile = f == c->tuned.end() ? 0 : f->second;
+    *tile = f == c->tuned.end() ? 0 : f->second.first;
+    return EAPDTW_OK;
+}
+
+int32_t eapdtw_set_tuning(eapdtw_ctx* c, int32_t log2_m, int32_t ratio_tenths, int32_t band, int32_t tile,
+                          int32_t check_double) {
+    if (!c || log2_m < 0 || log2_m > 12 || ratio_tenths < 0 || ratio_tenths > 10 || band < 0 || band > 1)
+        return EAPDTW_ERR_INVALID_ARG;
+    if ((tile != 0 && tile != 4 && tile != 8 && tile != 16 && tile != 32) || check_double < 0 || check_double > 1)
+        return EAPDTW_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(c->mu);
+    const auto key = std::make_tuple(static_cast<int>(log2_m), static_cast<int>(ratio_tenths), static_cast<int>(band));
+    if (tile == 0 && check_double == 0) c->tuned.erase(key);
+    else c->tuned[key] = std::make_pair(static_cast<int>(tile), static_cast<int>(check_double));
+    return EAPDTW_OK;
+}
+
+int32_t eapdtw_get_tuning(eapdtw_ctx* c, int32_t log2_m, int32_t ratio_tenths, int32_t band, int32_t* tile,
+                          int32_t* check_double) {
+    if (!c || !tile || !check_double) return EAPDTW_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(c->mu);
+    auto f = c->tuned.find(std::make_tuple(static_cast<int>(log2_m), static_cast<int>(ratio_tenths), static_cast<int>(band)));
+    *tile = f == c->tuned.end() ? 0 : f->second.first;
+    *check_double = f == c->tuned.end() ? 0 : f->second.second;
     return EAPDTW_OK;
 }
 
@@ -845,25 +875,27 @@ int32_t eapdtw_autotune(eapdtw_ctx* c, const eapdtw_item* items, int32_t n, int6
         const int base = 4 << first_level(c, m, w);
         const int cand[3] = {base, base * 2, base / 2};
         float best_ms = INFINITY;
-        int best_K = base;
-        for (int K : cand) {
-            if (K < 4 || K > 32) continue;
-            c->tuned[kv.first] = K;
-            float ms = 0.0f, ms2 = 0.0f;
-            rc = run_batch(c, &it, 1, it.k, d_idx, d_dist, nullptr, stream, &len, &ms);   // warm-up
-            if (rc == EAPDTW_OK) rc = run_batch(c, &it, 1, it.k, d_idx, d_dist, nullptr, stream, &len, &ms2);
-            if (rc != EAPDTW_OK) break;
-            ms = std::min(ms, ms2);
-            if (ms < best_ms) {
-                best_ms = ms;
-                best_K = K;
+        std::pair<int, int> best(base, 0);
+        for (int chk = 0; chk < 2 && rc == EAPDTW_OK; ++chk) {
+            for (int K : cand) {
+                if (K < 4 || K > 32) continue;
+                c->tuned[kv.first] = std::make_pair(K, chk);
+                float ms = 0.0f, ms2 = 0.0f;
+                rc = run_batch(c, &it, 1, it.k, d_idx, d_dist, nullptr, stream, &len, &ms);   // warm-up
+                if (rc == EAPDTW_OK) rc = run_batch(c, &it, 1, it.k, d_idx, d_dist, nullptr, stream, &len, &ms2);
+                if (rc != EAPDTW_OK) break;
+                ms = std::min(ms, ms2);
+                if (ms < best_ms) {
+                    best_ms = ms;
+                    best = std::make_pair(K, chk);
+                }
             }
         }
         if (rc != EAPDTW_OK) {
             c->tuned.erase(kv.first);
             break;
         }
-        c->tuned[kv.first] = best_K;
+        c->tuned[kv.first] = best;
         ++tuned;
     }
     dfree(d_idx);

@@ -98,8 +98,10 @@ struct eapdtw_ctx {
     std::mutex mu;             // guards everything below except the server's own state
     std::vector<eapdtw::RefEntry> refs;
     eapdtw::Arena batch;
-    // K of the first level per (log2 m, window ratio in tenths, band mode), set by the autotuner
-    std::map<std::tuple<int, int, int>, int> tuned;
+    // per (log2 m, window ratio in tenths, band mode), set by the autotuner: the
+    // first level's K (0: the built-in rule) and the check-interval choice
+    // (1: twice the wavefront's built-in interval)
+    std::map<std::tuple<int, int, int>, std::pair<int, int>> tuned;
     int64_t batches = 0, items_run = 0, items_rerun = 0;
     eapdtw::Server* server = nullptr;
 };
@@ -125,6 +127,7 @@ struct PlannedItem {
 // Planning helpers (the caller holds ctx->mu).
 std::tuple<int, int, int> signature(int m, int w);
 int first_level(const eapdtw_ctx* c, int m, int w);
+int check_choice(const eapdtw_ctx* c, int m, int w);   // 1: twice the built-in check interval
 int band_mode(int level, int w, bool unconstrained);
 int env_level(int radius);
 int32_t ensure_env(eapdtw_ctx* c, RefEntry& r, int p, cudaStream_t st);

@@ -116,11 +116,15 @@ __device__ __forceinline__ float f_nan() { return __int_as_float(0x7fffffff); }
 // paper's); kCostAbsolute, |a - b| (another elastic distance with the same
 // recurrence, Section 6).  Both are non-negative, so the pruning and abandoning
 // arguments hold unchanged.
+// check2: 1 checks borders and the bound at twice the built-in interval (the
+// autotuner's poll-interval choice; the retirement and switch-on margins grow
+// with it), 0 at the built-in one.  Results are the same either way.
 template <int K, int BAND, int J = 1, bool CS = false, bool TIGHT = false, int COST = 0>
 __device__ __forceinline__ DtwOut dtw_warp(const float* __restrict__ rows, float a, float cw,
                                            float isd, const float* __restrict__ cols, int nr,
                                            int nc, int w, const BestSoFar bsf, float ub,
-                                           int* dbg = nullptr, const float* __restrict__ cb = nullptr) {
+                                           int* dbg = nullptr, const float* __restrict__ cb = nullptr,
+                                           int check2 = 0) {
     static_assert(K % 4 == 0, "K must be a multiple of 4");
     static_assert(J >= 1 && J <= 4, "1 to 4 windows");
     (void)dbg;
@@ -173,6 +177,10 @@ __device__ __forceinline__ DtwOut dtw_warp(const float* __restrict__ rows, float
     // ub = +inf, a +inf cell would otherwise count as alive.
     ub = fminf(ub, 3.402823466e38f);
     constexpr int kCE = (J == 1 && BAND == 0) ? kCheckEveryOne : kCheckEvery;   // steps between checks
+    // lanes 31-ce .. 31 for the effective interval ce: an alive cell there can
+    // reach the window's end before the next check
+    const int ce_eff = check2 ? 2 * kCE : kCE;
+    const unsigned near_mask = ce_eff >= 31 ? kFull : (kFull << (31 - ce_eff));
     // The bound read at the last check, applied at the next one (its loads
     // complete meanwhile).
     BestSoFar::Raw ub_raw = BestSoFar::of(ub);
@@ -298,12 +306,12 @@ __device__ __forceinline__ DtwOut dtw_warp(const float* __restrict__ rows, float
         // step s or s-1 one block to its left at most, so with nothing alive
         // in lanes 31-kCE..31 at steps t-1 and t, nothing alive reaches the
         // last lane before the next check.
-        if (J == 1 && d > 0 && (~(dead_a[0] & db[0]) & (kFull << (31 - kCE))) == 0) d = 0;
+        if (J == 1 && d > 0 && (~(dead_a[0] & db[0]) & near_mask) == 0) d = 0;
         // Switch the next window on when an alive cell came within 9 blocks
         // of the end of the last active one; off when the last one and the
         // end of the one before are dead.
         if (J > 1) {
-            constexpr unsigned kNear = 0xff800000u;  // lanes 23..31
+            const unsigned kNear = near_mask;   // lanes 31-ce .. 31 (23..31 at 8 steps)
             unsigned near_last = 0, near_prev = 0, dead_last = 0;
 #pragma unroll
             for (int j = 0; j < J; ++j) {
@@ -391,6 +399,7 @@ __device__ __forceinline__ DtwOut dtw_warp(const float* __restrict__ rows, float
 #pragma unroll
             for (int j = 0; j < J; ++j)
                 dead_a[j] = (j < jact) ? __ballot_sync(kFull, !(bmin_a[j] <= thr(j, t - 1))) : kFull;
+            if (check2 && (t & kCE)) continue;   // every other check is skipped
             if (check(bmin_b, t)) break;
             continue;
         }
@@ -440,7 +449,7 @@ __device__ __forceinline__ DtwOut dtw_warp(const float* __restrict__ rows, float
 #pragma unroll
             for (int j = 0; j < J; ++j)
                 dead_a[j] = (j < jact) ? __ballot_sync(kFull, !(bmin[j] <= thr(j, t))) : kFull;
-        } else if (phase == 0) {
+        } else if (phase == 0 && !(check2 && (t & kCE))) {
             if (check(bmin, t)) break;
         }
     }

@@ -104,6 +104,7 @@ struct TileCtx {
     int* lost;            // set to 1 when an overflow entry did not fit the list (or nullptr)
     float* cbw;           // this warp's scratch for upper-bound tightening (>= m + 1 floats), or nullptr
     float* zr;            // elastic wavefront: this warp's row buffer (row 1 at zr[0], NaN pads around)
+    int check2;           // one-window wavefront: 1 checks at twice its built-in interval (the autotuner's choice)
     int* dbg;
 };
 
@@ -343,7 +344,7 @@ __device__ __forceinline__ void process_tile(const TileCtx& C, float* s_r, bool 
         } else {
             constexpr int kJ = JW > 0 ? JW : dtw_windows(K, BAND);
             o = dtw_warp<K, BAND, kJ, (JW > 0), TIGHT, COST>(s_r + off, a_s, cw_s, isd_s, C.zq, m, m, C.w, C.bsf,
-                                                             ub, C.dbg, TIGHT ? C.cbw : nullptr);
+                                                             ub, C.dbg, TIGHT ? C.cbw : nullptr, C.check2);
         }
         if (lane == 0) {
             count(kCntSteps, static_cast<unsigned long long>(o.steps));
@@ -458,6 +459,7 @@ search_kernel(const SearchArgs A) {
     C.lost = nullptr;
     C.cbw = A.cb ? A.cb + (static_cast<int64_t>(blockIdx.x) * (blockDim.x >> 5) + warp) * A.cb_stride : nullptr;
     C.zr = nullptr;
+    C.check2 = 0;
     C.dbg = A.dbg;
 
     for (;;) {
@@ -569,6 +571,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, EAPDTW_MINB_ELASTIC) sear
     C.lost = nullptr;
     C.cbw = nullptr;
     C.zr = s_rows + kElPadRows;
+    C.check2 = 0;
     C.dbg = A.dbg;
 
     for (;;) {

@@ -204,15 +204,38 @@ def test_autotune_keeps_results():
 def test_tuning_table_round_trip(tmp_path):
     with api.Context(0) as ctx:
         ctx.set_first_tile(7, 3, 1, 16)
-        ctx.set_first_tile(10, 10, 0, 8)
-        assert ctx.tuning_table() == {(7, 3, 1): 16, (10, 10, 0): 8}
+        ctx.set_tuning(10, 10, 0, 8, 1)
+        ctx.set_tuning(9, 5, 1, 0, 1)      # the check interval alone
+        assert ctx.tuning_table() == {(7, 3, 1): (16, 0), (10, 10, 0): (8, 1), (9, 5, 1): (0, 1)}
+        assert ctx.get_first_tile(10, 10, 0) == 8
         path = str(tmp_path / "tuning.json")
         ctx.save_tuning(path)
     with api.Context(0) as ctx2:
-        assert ctx2.load_tuning(path) == 2
-        assert ctx2.tuning_table() == {(7, 3, 1): 16, (10, 10, 0): 8}
+        assert ctx2.load_tuning(path) == 3
+        assert ctx2.tuning_table() == {(7, 3, 1): (16, 0), (10, 10, 0): (8, 1), (9, 5, 1): (0, 1)}
         ctx2.set_first_tile(7, 3, 1, 0)
-        assert ctx2.tuning_table() == {(10, 10, 0): 8}
+        ctx2.set_tuning(9, 5, 1, 0, 0)
+        assert ctx2.tuning_table() == {(10, 10, 0): (8, 1)}
+
+
+def test_doubled_check_interval_changes_work_not_results():
+    """Every signature of a mixed batch at twice the wavefront's check interval:
+    bit-identical to the built-in interval (and so to the one-query path)."""
+    rng = np.random.default_rng(23)
+    R_np = np.asarray(synth.random_walk(60_000, 24), np.float32)
+    with api.Context(0) as ctx:
+        R = dev(R_np)
+        rid = ctx.register(R)
+        items = mixed_items(rng, [(rid, R_np)], 6, 64, 1300, 1000)
+        Qd = {id(t[0]): dev(t[0]) for t in items}
+        dev_items = [(Qd[id(t[0])],) + t[1:] for t in items]
+        bi0, bd0 = ctx.search_batch(dev_items, 5)
+        for lg in range(13):
+            for tenth in range(11):
+                for band in (0, 1):
+                    ctx.set_tuning(lg, tenth, band, 0, 1)
+        bi1, bd1 = ctx.search_batch(dev_items, 5)
+        assert torch.equal(bd0, bd1) and torch.equal(bi0, bi1)
 
 
 def test_batched_mix_sample_against_the_oracle():
