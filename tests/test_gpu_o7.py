@@ -74,3 +74,27 @@ def test_batched_results_bit_exact():
             k = len(ei)
             np.testing.assert_array_equal(bd[j, :k], ed)
             np.testing.assert_array_equal(bi[j, :k], ei)
+
+
+@pytest.mark.parametrize("kind,m,seed", [("walk", 1024, 11), ("ecg", 512, 12)])
+def test_dominant_shape_audit_counts_bit_exact(kind, m, seed):
+    """The benchmark's dominant path: an unconstrained search without lower
+    bounds (the elastic first level and its re-run levels), and the same search
+    with the first level forced to the one-window wavefront at K = 16.  Under a
+    fixed bound just above the FP64 oracle's nearest-neighbour distance, the
+    audit counts and the k-best list equal the FP32 emulation's bit for bit,
+    and the free search returns the emulation's nearest window (4,001 windows,
+    so that the emulation of every window's DTW finishes)."""
+    R, Q = inputs(kind, 4_000 + m, m, seed)
+    _, od, _ = O.search_cascade(Q, R, m, 1, nthreads=8)
+    ub = float(np.float32(od[0] * (1 + 1e-4)))
+    ai, ad, oc = O.o7_search(Q, R, m, 3, audit_ub=ub, use_lb=False)
+    assert oc["dtw_completed"] >= 1
+    Rd, Qd = dev(R), dev(Q)
+    for tile in (0, 16):
+        gi, gd = api.subseq_search(Qd, Rd, m, 1, no_lb=True, tile=tile)
+        assert float(gd.cpu()[0]) == ad[0] and int(gi.cpu()[0]) == ai[0], (tile, gi, gd, ai, ad)
+        gi2, gd2, gc = api.subseq_search(Qd, Rd, m, 3, audit_ub=ub, no_lb=True, tile=tile, return_counters=True)
+        assert {c: gc[c] for c in AUDIT_KEYS} == oc, (tile, gc, oc)
+        np.testing.assert_array_equal(gd2.cpu().numpy(), ad)
+        np.testing.assert_array_equal(gi2.cpu().numpy(), ai)
