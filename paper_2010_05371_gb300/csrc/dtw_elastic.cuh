@@ -88,6 +88,14 @@ __host__ __device__ inline int elastic_col_floats(int m) { return (m + kElPadCol
 // Cells one busy lane-step computes.
 constexpr int kElCellsPerStep = kElK * kElR;
 
+// Rows written ahead of the steps that read them (a multiple of 32; a
+// compile-time knob for tuning experiments).
+#ifndef EAPDTW_ELASTIC_FILL
+#define EAPDTW_ELASTIC_FILL 64
+#endif
+constexpr int kElFillRows = EAPDTW_ELASTIC_FILL;
+static_assert(kElFillRows >= 32 && kElFillRows % 32 == 0, "whole warps of rows");
+
 // zr: minus row r (1-based), -z_r, at zr[r - 1] (so that d = q + (-z) is one
 // add, packed or not), NaN at zr[-kElPadRows .. -1] and
 // zr[nr .. nr + kElPadRows + 2); zq: column c at zq[c - 1], NaN from zq[nc]
@@ -95,13 +103,19 @@ constexpr int kElCellsPerStep = kElK * kElR;
 // with identical arguments.  Returns busy = lane-steps executed by the
 // active windows (started or not).
 //
+// The rows are written on demand: fill(r0, r1), called by all lanes with
+// identical arguments, writes zr[r0 .. r1) and synchronises the warp.  Steps
+// up to s read rows below 2 s only, and most candidates are abandoned long
+// before their last row, so the rows are filled kElFillRows at a time before
+// the interval that first reads them.
+//
 // The steps and the check between them are compiled once per number of
 // active windows (1..J), so that a step computes only the active windows and
 // inactive ones hold no live state: a window's state is reset when it is
 // switched on.
-template <int J, int COST>
+template <int J, int COST, typename FillF>
 __device__ __forceinline__ DtwOut dtw_elastic(const float* __restrict__ zr, const float* __restrict__ zq, int nr,
-                                              int nc, const BestSoFar bsf, float ub) {
+                                              int nc, const BestSoFar bsf, float ub, FillF fill) {
     constexpr int K = kElK;
     constexpr int CE = kElCE;
     const int lane = threadIdx.x & 31;
@@ -142,6 +156,20 @@ __device__ __forceinline__ DtwOut dtw_elastic(const float* __restrict__ zr, cons
             const int o = -2 * (1 + B0 + 32 * j + lane);
             const int cap = nre - 2 * (tnow + 1);
             zp[j] = zr + (o < cap ? o : cap);
+        }
+    };
+    // rows below `filled` are written; the steps of an interval starting after
+    // step t read rows below 2 (t + CE)
+    int filled = nr < kElFillRows ? nr : kElFillRows;
+    fill(0, filled);
+    auto fill_to = [&](int need) {
+        if (need > nr) need = nr;
+        if (need > filled) {
+            int to = filled + kElFillRows;
+            to = to > need ? to : need;
+            to = to < nr ? to : nr;
+            fill(filled, to);
+            filled = to;
         }
     };
     reset(0);
@@ -314,6 +342,7 @@ __device__ __forceinline__ DtwOut dtw_elastic(const float* __restrict__ zr, cons
 
     for (;;) {
         if (t + CE < t_end) {
+            fill_to(2 * (t + CE));
             int r;
             if (jact == 1) r = interval(std::integral_constant<int, 1>{});
             else if (J >= 2 && jact == 2) r = interval(std::integral_constant<int, (J >= 2 ? 2 : 1)>{});
@@ -330,6 +359,7 @@ __device__ __forceinline__ DtwOut dtw_elastic(const float* __restrict__ zr, cons
         // block bm passes it on.  If that block lies beyond the active windows
         // no alive value ever reached it (the switch-on rule): the result is +inf.
         const int src = bm - B0;
+        fill_to(nr);
         for (int s = t + 1; s <= t_end; ++s) {
             float l0[J], l1[J];
 #pragma unroll

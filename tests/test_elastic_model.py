@@ -9,7 +9,8 @@ NaN columns after the query's, checks every 8 steps (all blocks dead at two
 consecutive steps abandons; retirable leading blocks; windows switched on
 when an alive block comes within 9 blocks of the end of the last one, off when
 they are no longer needed; lazy slides; an overflow when J windows do not
-suffice), and the final step's capture of cell (nr, nc).  It asserts every
+suffice), the rows written on demand 64 at a time before the interval that
+first reads them, and the final step's capture of cell (nr, nc).  It asserts every
 index it reads from the row and column buffers, as the kernel's shared-memory
 buffers are sized, and its outcomes must agree with Eq. 1-5 (the oracle's DTW):
 a finished value equals DTW when DTW <= ub, an abandoned candidate has
@@ -87,6 +88,13 @@ def emu(rows, cols, ub, J=3, ub_sched=None, CE=CE):
             zoff[j] = np.minimum(o, nre - 2 * (tnow + 1))
 
     set_zoff(0)
+    FILL = 64   # rows written ahead (the kernel's kElFillRows)
+    fl = {"filled": min(nr, FILL)}
+
+    def fill_to(need):
+        need = min(need, nr)
+        if need > fl["filled"]:
+            fl["filled"] = min(nr, max(need, fl["filled"] + FILL))
 
     def cost(qv, nz, mn):
         d = (qv + nz).astype(f32)
@@ -108,6 +116,9 @@ def emu(rows, cols, ub, J=3, ub_sched=None, CE=CE):
         for j in range(jact):
             idx = zoff[j] + 2 * s
             assert (padr + idx).min() >= 0 and (padr + idx + 1).max() < rowf, ("row read", idx.min(), idx.max())
+            for r in (idx, idx + 1):   # a row inside the window's rows has been written
+                inside = (r >= 0) & (r < nr)
+                assert np.all(r[inside] < fl["filled"]), ("row read before it was written", r.max(), fl["filled"])
             z0 = zr[padr + idx]; z1 = zr[padr + idx + 1]
             a0 = cost(q[j, :, 0], z0, fmin3(p[j, :, 0], dg[j], l0[j]))
             a1 = cost(q[j, :, 1], z0, fmin3(p[j, :, 1], p[j, :, 0], a0))
@@ -130,6 +141,7 @@ def emu(rows, cols, ub, J=3, ub_sched=None, CE=CE):
     while True:
         jact = st["jact"]
         if t + CE < t_end:
+            fill_to(2 * (t + CE))
             bma = np.full((J, 32), INF, f32); bmb = np.full((J, 32), INF, f32)
             for s in range(1, CE + 1):
                 step(t + s, 1 if s == CE - 1 else (2 if s == CE else 0), -1, bma, bmb, None)
@@ -187,6 +199,7 @@ def emu(rows, cols, ub, J=3, ub_sched=None, CE=CE):
                 set_zoff(t)
             continue
         src = bm - st["B0"]
+        fill_to(nr)
         fin = np.full(32, INF, f32)
         for s in range(t + 1, t_end + 1):
             step(s, 0, src if (s == t_end and src >= 0) else -1, None, None, fin)
