@@ -44,7 +44,8 @@ extern "C" {
 #define EAPDTW_ERR_NAN_INPUT -2     /* a NaN or Inf in an input series */
 #define EAPDTW_ERR_OUT_OF_MEMORY -3 /* scratch allocation failed */
 #define EAPDTW_ERR_CUDA -4          /* a CUDA runtime call failed */
-#define EAPDTW_ERR_TIMEOUT -5       /* reserved: no call of this build waits on the device with a budget */
+#define EAPDTW_ERR_TIMEOUT -5       /* a device-side wait ran out: the widest level's warps wait on their
+                                       neighbours with a bounded number of polls; the results are void */
 #define EAPDTW_ERR_UNSUPPORTED -6   /* size beyond what this build supports (see each call) */
 #define EAPDTW_ERR_INTERNAL -7      /* a device-side consistency check failed */
 #define EAPDTW_ERR_BUSY -8          /* the object is in use (a reference read by the serving loop; a second server) */

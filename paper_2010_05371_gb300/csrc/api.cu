@@ -233,6 +233,7 @@ int32_t search_impl(Scratch& S, const float* Q, int64_t lQ, const float* R, int6
     a.lb_scale = kLbScale;
     a.counters = S.counters();
     a.dbg = ints + kDbgSlot;
+    a.err = ints + kTimeout;
     a.cb = tighten ? S.cb : nullptr;
     a.cb_stride = cb_stride;
 
@@ -359,6 +360,7 @@ int32_t search_impl(Scratch& S, const float* Q, int64_t lQ, const float* R, int6
     }
 #endif
     if (hi[kBad]) return EAPDTW_ERR_NAN_INPUT;
+    if (hi[kTimeout]) return EAPDTW_ERR_TIMEOUT;
     for (int lev = 0; lev + 1 < plan.nlev; ++lev)
         if (hi[kOvf0 + lev] > S.cap_ovf) return EAPDTW_ERR_INTERNAL;
     if (hi[kOvf0 + plan.nlev - 1] > 0) return EAPDTW_ERR_UNSUPPORTED;
@@ -385,7 +387,7 @@ const char* eapdtw_strerror(int32_t code) {
         case EAPDTW_ERR_NAN_INPUT: return "NaN or Inf in an input series";
         case EAPDTW_ERR_OUT_OF_MEMORY: return "out of device memory";
         case EAPDTW_ERR_CUDA: return "CUDA runtime error";
-        case EAPDTW_ERR_TIMEOUT: return "reserved (device wait timed out)";
+        case EAPDTW_ERR_TIMEOUT: return "a device-side wait ran out";
         case EAPDTW_ERR_UNSUPPORTED: return "size not supported by this build";
         case EAPDTW_ERR_INTERNAL: return "internal consistency check failed";
         case EAPDTW_ERR_BUSY: return "in use";

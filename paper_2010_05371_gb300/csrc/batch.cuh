@@ -33,6 +33,9 @@ constexpr int kAllClasses = kBatchClasses + kSeedClasses;
 constexpr int kBatchSeedBest = 32;   // sampled windows per item run through exact DTW
 constexpr int kBatchSeedSamples = 4096;
 constexpr int kBatchSlots = 64;      // k-best slots per item (k <= 64)
+// Bits of an item's flags.
+constexpr int kFlagLost = 1;         // an overflow entry did not fit a re-run list
+constexpr int kFlagTimeout = 2;      // a device-side wait of the group level ran out
 // Query copies of the widest levels (JW windows of 32 blocks of 32 columns).
 __host__ __device__ constexpr int wide_cols(int JW) { return JW * 1024; }
 __host__ __device__ constexpr size_t wide_smem(int JW) { return sizeof(float) * kWarpsPerBlock * wide_cols(JW); }
@@ -97,7 +100,7 @@ struct BatchDev {
     float* ub_seed;              // [cap_states]
     int* nbest;                  // [cap_states]
     long long* best;             // [cap_states * kBatchSeedBest]
-    int* flags;                  // [cap_states] bit 0: an overflow entry was lost
+    int* flags;                  // [cap_states] kFlagLost | kFlagTimeout
     unsigned long long* cost;    // [cap_states] SM clock cycles the warps spent on the state's
                                  // work units in this launch sequence (the serving loop's cost estimate)
     float* seed_ed;              // [cap_samples]

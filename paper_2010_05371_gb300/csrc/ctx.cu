@@ -574,9 +574,11 @@ int32_t run_batch(eapdtw_ctx* c, const eapdtw_item* items, int32_t n, int32_t ks
     if (counters) {
         for (int j = 0; j < EAPDTW_NCOUNTERS; ++j) counters[j] = j < 10 ? static_cast<int64_t>(hc[j]) : 0;
     }
+    for (int i = 0; i < n; ++i)
+        if (hf[i] & kFlagTimeout) return EAPDTW_ERR_TIMEOUT;
     // items that lost a re-run entry (a list was full): run them alone
     for (int i = 0; i < n; ++i) {
-        if (!(hf[i] & 1)) continue;
+        if (!(hf[i] & kFlagLost)) continue;
         const eapdtw_item& it = items[i];
         const RefEntry& r = c->refs[it.ref_id];
         eapdtw_search_opts o{};

@@ -136,6 +136,7 @@ extern "C" int32_t subseq_search_noalloc(const float* Q, int64_t lQ, const float
     a.use_lb = 1;
     a.lb_scale = 1.0001f;
     a.counters = counters;
+    a.err = ints + kTimeout;
     if (nw >= 2048) {
         const int ns = static_cast<int>(nw < kSeedN ? nw : kSeedN);
         CKN(launch_seed(a.ref, zq, m, nw, ns, seed_ed, seed_idx, k, ub_seed, seed_best, kSeedBest,
@@ -182,6 +183,7 @@ extern "C" int32_t subseq_search_noalloc(const float* Q, int64_t lQ, const float
     CKN(cudaMemcpyAsync(hi, ints, sizeof(hi), cudaMemcpyDeviceToHost, st));
     CKN(cudaStreamSynchronize(st));
     if (hi[kBad]) return EAPDTW_ERR_NAN_INPUT;
+    if (hi[kTimeout]) return EAPDTW_ERR_TIMEOUT;
     if (hi[kOvf0 + nlev - 1] > 0) return EAPDTW_ERR_UNSUPPORTED;
     return EAPDTW_OK;
 }

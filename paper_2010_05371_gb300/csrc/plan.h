@@ -85,9 +85,10 @@ enum IntSlot : int {
     kSeedOvf = kNBest + 1,
     kWorkTail = kSeedOvf + 1,               // probe: entries of the sample list; kWorkTail + 1: its work counter
     kProbeCount = kWorkTail + 2,            // overflows among the probe's windows
+    kTimeout = kProbeCount + 1,             // 1: a device-side wait of the group level ran out
     kDbgSlot = 24,                          // 24.. hold the device self-check record
     kNumInts = 32
 };
-static_assert(kProbeCount < kDbgSlot, "int slots overlap the device self-check record");
+static_assert(kTimeout < kDbgSlot, "int slots overlap the device self-check record");
 
 }  // namespace eapdtw

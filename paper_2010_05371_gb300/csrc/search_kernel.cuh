@@ -54,6 +54,7 @@ struct SearchArgs {
     int gate_threshold;
     int gate_wider;
     int* dbg;                 // device self-check record (EAPDTW_DEVICE_CHECKS builds only)
+    int* err;                 // set to 1 when a device-side wait ran out (the group level), or nullptr
 };
 
 __host__ __device__ inline int query_pad(int m) { return (m + kLbUnroll - 1) / kLbUnroll * kLbUnroll; }
@@ -335,11 +336,15 @@ __device__ __forceinline__ void process_tile(const TileCtx& C, float* s_r, bool 
         if constexpr (EL) {
             static_assert(BAND == 0 && !TIGHT, "the elastic wavefront is unconstrained, without tightening");
             // the window's z-normalised rows, negated, into the warp's buffer
-            // (the same znorm1 values the other wavefront computes row by row)
+            // as the wavefront reaches them (the same znorm1 values the other
+            // wavefront computes row by row)
             const float* xw = s_r + off;
-            for (int i = lane; i < m; i += 32) C.zr[i] = -znorm1(xw[i], a_s, cw_s, isd_s);
-            __syncwarp();
-            o = dtw_elastic<kElJ, COST>(C.zr, C.zq, m, m, C.bsf, ub);
+            float* zr = C.zr;
+            auto fill = [&](int r0, int r1) {
+                for (int i = r0 + lane; i < r1; i += 32) zr[i] = -znorm1(xw[i], a_s, cw_s, isd_s);
+                __syncwarp();
+            };
+            o = dtw_elastic<kElJ, COST>(C.zr, C.zq, m, m, C.bsf, ub, fill);
             __syncwarp();   // every lane is done with the rows before the next survivor's
         } else {
             constexpr int kJ = JW > 0 ? JW : dtw_windows(K, BAND);

@@ -214,6 +214,7 @@ int32_t Server::round(std::vector<Request*>& act) {
     int qi = 0;
     std::vector<Request*> lost;
     std::vector<char> bad(act.size(), 0);
+    std::vector<char> tmo(act.size(), 0);
     {
         std::lock_guard<std::mutex> lk(mu);
         ++rounds;
@@ -224,7 +225,11 @@ int32_t Server::round(std::vector<Request*>& act) {
                 r->next = r->nw;
             }
             r->started = true;
-            r->lost |= (hf[r->state] & 1) != 0;
+            if (hf[r->state] & kFlagTimeout) {   // a device-side wait ran out: the request fails
+                tmo[i] = 1;
+                r->next = r->nw;
+            }
+            r->lost |= (hf[r->state] & kFlagLost) != 0;
             windows += P[i].b.nwin;
             // cost per window: this round's measurement, smoothed over rounds
             // (the first round also prepared the query and ran the seeds)
@@ -236,7 +241,7 @@ int32_t Server::round(std::vector<Request*>& act) {
             if (r->next >= r->nw) {
                 std::memcpy(r->idx, A.hres_idx + i * EAPDTW_MAX_K, sizeof(int64_t) * r->k);
                 std::memcpy(r->dist, A.hres_dist + i * EAPDTW_MAX_K, sizeof(double) * r->k);
-                if (r->lost && !bad[i]) lost.push_back(r);
+                if (r->lost && !bad[i] && !tmo[i]) lost.push_back(r);
             }
         }
     }
@@ -248,7 +253,7 @@ int32_t Server::round(std::vector<Request*>& act) {
         for (size_t i = 0; i < act.size(); ++i) {
             Request* r = act[i];
             if (r->next < r->nw) continue;
-            int32_t rs = bad[i] ? EAPDTW_ERR_NAN_INPUT : EAPDTW_OK;
+            int32_t rs = bad[i] ? EAPDTW_ERR_NAN_INPUT : (tmo[i] ? EAPDTW_ERR_TIMEOUT : EAPDTW_OK);
             for (size_t j = 0; j < lost.size(); ++j)
                 if (lost[j] == r && lost_rc[j] != EAPDTW_OK) rs = lost_rc[j];
             r->t_done = Clock::now();
