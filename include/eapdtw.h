@@ -147,7 +147,8 @@ int32_t subseq_search(const float* Q, int64_t lQ, const float* R, int64_t lR, in
 /* Options of subseq_search_ex (zero-initialise, then set fields). */
 typedef struct {
     int32_t no_lb;        /* 1: skip LB_Kim / LB_Keogh ("nolb" variant of Section 5) */
-    int32_t tile;         /* DP cells per lane per step (4, 8, 16, 32); 0 = automatic */
+    int32_t tile;         /* first level: DP cells per lane per step (4, 8, 16, 32), 512 = a group of
+                             warps per candidate (512 columns per warp, lQ <= 4096); 0 = automatic */
     int32_t no_seed;      /* 1: start from ub = +inf instead of a sampled seed */
     int32_t audit;        /* 1: hold ub fixed at ub_fixed for the whole search */
     double ub_fixed;      /* used when audit = 1 */

@@ -42,7 +42,8 @@ def sources():
 # Sources compiled more than once, with the defines of each unit: each large
 # kernel instantiation gets its own nvcc process (see the files' headers).
 SPLIT_UNITS = {
-    "search_wide.cu": [[]] + [[f"-DEAPDTW_UNIT_BAND={b}", f"-DEAPDTW_UNIT_COST={c}"] for c in (0, 1) for b in (0, 1, 2)],
+    "search_wide.cu": [[]] + [[f"-DEAPDTW_UNIT_BAND={b}", f"-DEAPDTW_UNIT_LB={lb}", f"-DEAPDTW_UNIT_COST={c}"]
+                              for (lb, c) in ((0, 0), (1, 0), (0, 1)) for b in (0, 1, 2)],
     "batch_wide.cu": [[]] + [[f"-DEAPDTW_UNIT_LEVEL={lv}", f"-DEAPDTW_UNIT_BAND={b}"] for lv in (4, 5) for b in (0, 1, 2)],
     "pair_kernel.cu": [[], ["-DEAPDTW_UNIT_PAIR_WIDE"]],
     "search_k.cu": [[f"-DEAPDTW_UNIT_K={k}"] for k in (32, 16, 8, 4)],

@@ -254,7 +254,7 @@ int32_t search_impl(Scratch& S, const float* Q, int64_t lQ, const float* R, int6
         const int K = plan.K[plan.nlev - 1];
         const int bd = plan.band[plan.nlev - 1];
         if (plan.wide[plan.nlev - 1]) {
-            CK(launch_search_wide(bd, sa, search_blocks_wide(bd, m, cost) / 4 + 1, st, cost));
+            CK(launch_search_wide(bd, false, sa, search_blocks_wide(bd, false, m, cost) / 4 + 1, st, cost));
         } else {
             CK(launch_search(K, bd, false, sa, search_blocks(K, bd, false, m, false, cost) / 4 + 1, st, false, cost));
         }
@@ -278,7 +278,7 @@ int32_t search_impl(Scratch& S, const float* Q, int64_t lQ, const float* R, int6
         }
         const bool lb = use_lb && lev == 0;
         if (plan.wide[lev]) {
-            CK(launch_search_wide(plan.band[lev], la, search_blocks_wide(plan.band[lev], m, cost), st, cost));
+            CK(launch_search_wide(plan.band[lev], lb, la, search_blocks_wide(plan.band[lev], lb, m, cost), st, cost));
         } else if (plan.elastic[lev]) {
             CK(launch_search_elastic(lb, la, search_blocks_elastic(lb, m, cost), st, cost));
         } else if (lev == 0 && probe) {

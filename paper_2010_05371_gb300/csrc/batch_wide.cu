@@ -17,7 +17,7 @@ namespace eapdtw {
 __host__ __device__ constexpr int batch_group_warps(int level) { return level == 4 ? 4 : 8; }
 
 template <int BAND, int GW>
-__global__ void __launch_bounds__(kWarpsPerBlock * 32, 3) batch_group_kernel(const BatchLaunch L) {
+__global__ void __launch_bounds__(kWarpsPerBlock * 32, EAPDTW_MINB_GROUP) batch_group_kernel(const BatchLaunch L) {
     constexpr int kGroups = kWarpsPerBlock / GW;
     __shared__ GroupSync s_gs[kGroups];
     __shared__ unsigned long long s_cnt[kNumCounters];

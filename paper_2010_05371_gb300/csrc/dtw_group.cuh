@@ -53,7 +53,13 @@ constexpr int kGrpMaxWarps = 8;           // warps per group: up to 4096 columns
 constexpr int kGrpCE = 8;                 // steps between checks (and publications)
 constexpr int kGrpRing = 64;              // ring slots per warp (a power of 2)
 static_assert(kGrpRing > 2 * kGrpCE, "the producer may run kGrpRing - kGrpCE - 1 steps ahead");
-constexpr int kGrpSpinLimit = 1 << 22;    // polls per wait (about half a second)
+constexpr int kGrpSpinLimit = 1 << 23;    // polls per wait (about half a second)
+
+// Resident blocks per SM the group kernels are compiled for (a compile-time
+// knob for tuning experiments).
+#ifndef EAPDTW_MINB_GROUP
+#define EAPDTW_MINB_GROUP 3
+#endif
 
 // Warps a candidate of nc columns uses.
 __host__ __device__ constexpr int group_warps(int nc) { return (nc - 1) / kGrpCols + 1; }
@@ -66,7 +72,24 @@ struct GroupSync {
     int dead[kGrpMaxWarps];   // warp g's entries of steps >= dead[g] are dead or past the last row (INT_MAX: none)
     int abort_flag;           // a wait ran out: every warp leaves the candidate
     long long unit;           // the group's current work unit
+    // the tile's survivors of the lower-bound stage (lane bits) and their statistics
+    unsigned surv;
+    int cand;                 // the survivor the group runs next (-1: skipped by the recheck)
+    float ub;                 // the bound the leader read for it
+    float sa[32], scw[32], sisd[32], slb[32];
 };
+
+// Lane 31's store of v to a shared-memory float at the 32-bit shared address
+// a, as one predicated instruction (no branch around it).
+__device__ __forceinline__ void st_shared_lane31(unsigned a, float v, int lane) {
+    asm volatile("{\n\t.reg .pred p;\n\tsetp.eq.s32 p, %0, 31;\n\t@p st.volatile.shared.f32 [%1], %2;\n\t}"
+                 ::"r"(lane), "r"(a), "f"(v) : "memory");
+}
+__device__ __forceinline__ float ld_shared_volatile(unsigned a) {
+    float v;
+    asm volatile("ld.volatile.shared.f32 %0, [%1];" : "=f"(v) : "r"(a) : "memory");
+    return v;
+}
 
 // Ready for the next candidate: nothing written, nothing dead (one thread).
 __device__ __forceinline__ void group_reset(GroupSync& gs) {
@@ -93,7 +116,8 @@ __device__ __forceinline__ void group_bar(int gi, int nwarps) {
 
 // Warp g's part of the candidate.  All 32 lanes of each of the candidate's
 // group_warps(nc) warps call it with identical arguments (only g differs);
-// rows: the window's raw points (row r is znorm1(rows[r - 1], a, cw, isd));
+// rows: the window's raw points, in shared or global memory (row r is
+// znorm1(rows[r - 1], a, cw, isd));
 // cols: the z-normalised query (columns 1..nc); err: err_bit is or-ed into
 // it when a wait runs out.  The warp holding the last column returns the result (status 0,
 // or 2 when the group was aborted); the others return +inf with their steps
@@ -139,6 +163,11 @@ __device__ __forceinline__ DtwOut dtw_group(GroupSync& gs, int g, const float* _
     int busy = 0;
     int t = 0;               // last completed step
     DtwOut out{INF, 0, 0, 0};
+    const unsigned rin_s = static_cast<unsigned>(__cvta_generic_to_shared(&gs.ring[g > 0 ? g - 1 : 0][0]));
+    const unsigned rout_s = static_cast<unsigned>(__cvta_generic_to_shared(&gs.ring[g][0]));
+    auto put = [&](int s, float v) {   // lane 31's last column at step s into this warp's ring
+        st_shared_lane31(rout_s + 4u * static_cast<unsigned>(s & (kGrpRing - 1)), v, lane);
+    };
 
     // Polls until ready() (lane 0's reading, broadcast); false when the group
     // was aborted or this wait ran out (then the group is aborted).
@@ -154,7 +183,7 @@ __device__ __forceinline__ DtwOut dtw_group(GroupSync& gs, int g, const float* _
                     ok = 0;
                     break;
                 }
-                __nanosleep(64);
+                __nanosleep(32);
             }
         }
         return __shfl_sync(kFull, ok, 0) != 0;
@@ -162,9 +191,12 @@ __device__ __forceinline__ DtwOut dtw_group(GroupSync& gs, int g, const float* _
     // One step of this lane's block at row r (clamped into 1..nr for the
     // read: rows below 1 hold +inf state and inputs, rows past nr only feed
     // rows past nr); f1 positions the band's forced cells as in dtw_warp.
-    auto cells = [&](int r, float lin) {
+    auto row_at = [&](int r) -> float {   // shared or global memory
         const int rr = r < 1 ? 1 : (r > nr ? nr : r);
-        const float z = znorm1(__ldg(rows + rr - 1), a, cw, isd);
+        return rows[rr - 1];
+    };
+    auto cells = [&](int r, float x, float lin) {
+        const float z = znorm1(x, a, cw, isd);
         const int f1 = r - w - 1 - (b * K + 1);
         float diag = lprev;
         float left = lin;
@@ -221,9 +253,11 @@ __device__ __forceinline__ DtwOut dtw_group(GroupSync& gs, int g, const float* _
             __threadfence_block();
             dd = vs.dead[g - 1];
         }
-        const volatile float* rin = vs.ring[g > 0 ? g - 1 : 0];
-        auto input = [&](int s) -> float {   // lane 0's left input at step s (nothing at step 0)
-            return (s >= 2 && s - 1 < dd) ? rin[(s - 1) & (kGrpRing - 1)] : INF;
+        // lane 0's left input at step s (nothing at step 0); the slot is read
+        // unconditionally (it is in bounds) and the value selected
+        auto input = [&](int s) -> float {
+            const float v = ld_shared_volatile(rin_s + 4u * static_cast<unsigned>((s - 1) & (kGrpRing - 1)));
+            return (s >= 2 && s - 1 < dd) ? v : INF;
         };
         // room: warp g+1 has read the entries these steps overwrite (step
         // s reuses the slot of step s - kGrpRing, read before warp g+1
@@ -247,15 +281,21 @@ __device__ __forceinline__ DtwOut dtw_group(GroupSync& gs, int g, const float* _
             lprev = INF;
             if (lane < ns) vs.ring[g][(t + 1 + lane) & (kGrpRing - 1)] = INF;
         } else if (t_next < t_fin) {
-            // CE steps, no capture; lane 0's input read one step ahead
+            // CE steps, no capture; lane 0's input and each lane's row read
+            // one step ahead
             float nxt = input(t + 1);
+            float xn = row_at(t + 1 - b);
 #pragma unroll
             for (int s = 1; s <= CE; ++s) {
                 const float cur = nxt;
-                if (s < CE) nxt = input(t + s + 1);
+                const float x = xn;
+                if (s < CE) {
+                    nxt = input(t + s + 1);
+                    xn = row_at(t + s + 1 - b);
+                }
                 const float up = __shfl_up_sync(kFull, lout, 1);
-                cells(t + s - b, lane == 0 ? cur : up);
-                if (lane == 31) vs.ring[g][(t + s) & (kGrpRing - 1)] = lout;
+                cells(t + s - b, x, lane == 0 ? cur : up);
+                put(t + s, lout);
                 if (s == CE - 1) bmin_a = block_min();
                 if (s == CE) bmin_b = block_min();
             }
@@ -267,8 +307,8 @@ __device__ __forceinline__ DtwOut dtw_group(GroupSync& gs, int g, const float* _
             for (int s = t + 1; s <= t_next; ++s) {
                 const float in0 = input(s);
                 const float up = __shfl_up_sync(kFull, lout, 1);
-                cells(s - b, lane == 0 ? in0 : up);
-                if (lane == 31) vs.ring[g][s & (kGrpRing - 1)] = lout;
+                cells(s - b, row_at(s - b), lane == 0 ? in0 : up);
+                put(s, lout);
                 if (last && s == t_fin && b == bm) {
 #pragma unroll
                     for (int k = 0; k < K; ++k) fin = (k == km) ? prv[k] : fin;

@@ -38,8 +38,10 @@ cudaError_t launch_search(int K, int band, bool lb, const SearchArgs& args, int 
 int search_blocks(int K, int band, bool lb, int m, bool tight = false, int cost = 0);
 // The widest re-run level (K = 32, columns streamed from shared memory; two
 // windows, 2048 columns, for m <= 2048; four windows, 4096 columns, beyond).
-cudaError_t launch_search_wide(int band, const SearchArgs& args, int blocks, cudaStream_t s, int cost = 0);
-int search_blocks_wide(int band, int m, int cost = 0);
+// The group levels (search_wide.cu): lb = true runs tiles through the
+// lower-bound cascade (a first level), lb = false the list or tiles without it.
+cudaError_t launch_search_wide(int band, bool lb, const SearchArgs& args, int blocks, cudaStream_t s, int cost = 0);
+int search_blocks_wide(int band, bool lb, int m, int cost = 0);
 
 // The unconstrained first level with the narrow-block elastic wavefront
 // (search_elastic_kernel; tile mode only).

@@ -153,7 +153,7 @@ extern "C" int32_t subseq_search_noalloc(const float* Q, int64_t lQ, const float
         sa.counters = seed_counters;
         const int K = plan.K[nlev - 1], bd = plan.band[nlev - 1];
         if (plan.wide[nlev - 1]) {
-            CKN(launch_search_wide(bd, sa, search_blocks_wide(bd, m) / 4 + 1, st));
+            CKN(launch_search_wide(bd, false, sa, search_blocks_wide(bd, false, m) / 4 + 1, st));
         } else {
             CKN(launch_search(K, bd, false, sa, search_blocks(K, bd, false, m) / 4 + 1, st));
         }
@@ -171,7 +171,7 @@ extern "C" int32_t subseq_search_noalloc(const float* Q, int64_t lQ, const float
         }
         const bool lb = lev == 0;
         if (plan.wide[lev]) {
-            CKN(launch_search_wide(plan.band[lev], la, search_blocks_wide(plan.band[lev], m), st));
+            CKN(launch_search_wide(plan.band[lev], lb, la, search_blocks_wide(plan.band[lev], lb, m), st));
         } else if (plan.elastic[lev]) {
             CKN(launch_search_elastic(lb, la, search_blocks_elastic(lb, m), st));
         } else {

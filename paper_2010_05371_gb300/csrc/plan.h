@@ -9,24 +9,30 @@
 
 namespace eapdtw {
 
-constexpr int kMaxLevels = 4;   // levels 0..kMaxLevels (at most five: K = 4, 8, 16, 32, wide)
+constexpr int kMaxLevels = 4;   // levels 0..kMaxLevels (at most five: K = 4, 8, 16, 32, group)
 
 // Work levels: the first launch runs every window; windows whose live region
 // overflowed the previous level's window of blocks are re-run by the next one,
-// up to the widest (K = 32 with several windows of columns).
+// up to the widest (a group of warps holding every column).
 struct Plan {
     int nlev = 0;
     int K[kMaxLevels + 1];
     int band[kMaxLevels + 1];
-    bool wide[kMaxLevels + 1];      // K = 32, columns streamed, two or four windows
+    bool wide[kMaxLevels + 1];      // a group of warps per candidate (dtw_group.cuh): the widest level,
+                                    // or the first one (with the lower bounds) when the tile hint asks
     bool elastic[kMaxLevels + 1];   // the narrow-block elastic wavefront (unconstrained first level)
 };
 
+// Tile hint that makes the first level a group of warps (any query length).
+constexpr int kGroupTileHint = 512;
+
 // nr, nc: rows and columns of the DP (window and query lengths); w: the window
 // (w >= max(nr, nc) - 1 is unconstrained); tile_hint: 4, 8, 16 or 32 fixes the
-// first level's K, 0 chooses.  allow_elastic: the unconstrained first level
-// may use the elastic wavefront (it does not implement upper-bound tightening).
-inline Plan plan_levels(int64_t nr, int64_t nc, int64_t w, int tile_hint, bool allow_elastic = true) {
+// first level's K, kGroupTileHint makes it a group of warps, 0 chooses.
+// search_levels: the first level may be the elastic wavefront (unconstrained)
+// or, on request, a group of warps; neither implements upper-bound tightening,
+// and the pair kernel has neither.
+inline Plan plan_levels(int64_t nr, int64_t nc, int64_t w, int tile_hint, bool search_levels = true) {
     const int64_t lmax = nr > nc ? nr : nc;
     const bool unconstrained = w >= lmax - 1;
     Plan p;
@@ -34,11 +40,22 @@ inline Plan plan_levels(int64_t nr, int64_t nc, int64_t w, int tile_hint, bool a
     int k0 = 32;
     if (tile_hint == 4 || tile_hint == 8 || tile_hint == 16 || tile_hint == 32) {
         k0 = tile_hint;
+    } else if (search_levels && tile_hint == kGroupTileHint && nc <= 8 * 512) {
+        p.K[0] = 16;
+        p.band[0] = unconstrained ? 0 : (16 <= 2 * w + 2 ? 1 : 2);
+        p.wide[0] = true;
+        p.elastic[0] = false;
+        p.nlev = 1;
+        return p;
     } else if (!unconstrained) {
         // blocks spanned by the band across the pipelined rows, plus margin
         for (int K = 4; K <= 32; K *= 2)
             if ((2 * w + K) / (K + 1) + 3 <= 32) { k0 = K; break; }
-    } else if (allow_elastic && nc > 32 * 4) {
+        // A band that fits no warp's window still starts with one warp at
+        // K = 32: measured on GB300 a group of warps as the first level was
+        // slower (its warps wait on one another while the live region is
+        // narrower than the band), so the group only re-runs the overflows.
+    } else if (search_levels && nc > 32 * 4) {
         p.K[0] = kElK;
         p.band[0] = 0;
         p.wide[0] = false;
@@ -62,12 +79,14 @@ inline Plan plan_levels(int64_t nr, int64_t nc, int64_t w, int tile_hint, bool a
         ++p.nlev;
         covered = cols;
     }
-    // Last level: four windows of 32-column blocks (4096 columns), needed only
-    // when the columns do not fit one window of K = 32 (an empty re-run list
-    // makes it a no-op launch).
+    // Last level: a group of warps of blocks of 16 columns (up to 4096
+    // columns; the pair kernel's widest level: K = 32 with the columns
+    // streamed), needed only when the columns do not fit one window of K = 32
+    // (an empty re-run list makes it a no-op launch).
     if (nc > 32 * 32) {
-        p.K[p.nlev] = 32;
-        p.band[p.nlev] = unconstrained ? 0 : (32 <= 2 * w + 2 ? 1 : 2);
+        const int kw = search_levels ? 16 : 32;
+        p.K[p.nlev] = kw;
+        p.band[p.nlev] = unconstrained ? 0 : (kw <= 2 * w + 2 ? 1 : 2);
         p.wide[p.nlev] = true;
         p.elastic[p.nlev] = false;
         ++p.nlev;

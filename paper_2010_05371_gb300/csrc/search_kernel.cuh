@@ -148,56 +148,27 @@ __device__ __forceinline__ void tightening_terms(const TileCtx& C, const float* 
     __syncwarp();
 }
 
-// One work item on one warp: a tile of nlanes (<= 32) consecutive windows
-// starting at i0, or (list_mode) the single window i0.  STAGE: copy the
-// windows' points into the warp's shared-memory tile s_r first (one query per
-// launch); otherwise read them from the reference in global memory through L1
-// (a batch, whose query lengths differ from item to item).  Then the lower
-// bounds lane by lane (tile mode), then EAPrunedDTW for every survivor on the
-// whole warp.
-// ECM: where LB_Keogh EC reads the reference envelope: 1 = arrays over the
-// window's own radius; 2 = a sparse table of running maxima / minima (any
-// radius, two reads per bound; windows within the radius of either end of the
-// reference use a slightly wider envelope, which is still a valid bound).
-// JW: 0 = the DP columns' query values held in registers, one window of 32
-// blocks; JW >= 1 = the values streamed from C.zq at every step, JW windows of
-// 32 blocks (fewer registers per thread, more resident warps).
-// TIGHT: upper-bound tightening for the survivors (needs C.cbw and the lower
-// bounds; compiled out otherwise).
-// EL: run the survivors through the narrow-block elastic wavefront
-// (dtw_elastic.cuh; unconstrained, K = kElK, C.zr and C.zq padded as it needs).
-template <int K, int BAND, bool LB, int JW, bool STAGE = true, int ECM = 1, bool TIGHT = false, int COST = 0,
-          bool EL = false, typename CountF>
-__device__ __forceinline__ void process_tile(const TileCtx& C, float* s_r, bool list_mode, int64_t i0,
-                                             int nlanes, CountF count) {
+// The first half of process_tile: per-lane window statistics (a, cw, isd),
+// the lower-bound cascade (lb: the largest bound computed) with its counts,
+// and the corner check.  The tile's points are at s_r (window lane at
+// s_r + lane; list mode: the single window at s_r).  Returns whether this
+// lane's window is still alive.  All 32 lanes call it.
+template <int BAND, bool LB, int ECM, int COST, typename CountF>
+__device__ __forceinline__ bool tile_lanes(const TileCtx& C, const float* s_r, bool list_mode, int64_t i0, int nlanes,
+                                           CountF count, float& a, float& cw, float& isd, float& lb) {
     const int lane = threadIdx.x & 31;
     const int m = C.m;
     const int mp = query_pad(m);
-    const int len = nlanes - 1 + m;
-    if (!EAPDTW_CHECK(C.dbg, i0 >= 0 && i0 + len <= C.ref.n, 21, len)) return;
-    if (STAGE) {
-        // R[i0 .. i0 + nlanes - 1 + m) into the warp's tile.
-        if (!EAPDTW_CHECK(C.dbg, len <= tile_floats(m), 26, len)) return;
-        if ((reinterpret_cast<uintptr_t>(C.ref.R + i0) & 15) == 0 && !list_mode) {
-            const float4* src = reinterpret_cast<const float4*>(C.ref.R + i0);
-            const int nv = len / 4;
-            for (int v = lane; v < nv; v += 32) reinterpret_cast<float4*>(s_r)[v] = __ldg(src + v);
-            for (int j = nv * 4 + lane; j < len; j += 32) s_r[j] = __ldg(C.ref.R + i0 + j);
-        } else {
-            for (int j = lane; j < len; j += 32) s_r[j] = __ldg(C.ref.R + i0 + j);
-        }
-        __syncwarp();
-    } else {
-        s_r = const_cast<float*>(C.ref.R + i0);
-    }
-
+    (void)mp;
     // ---- per-lane window statistics and lower bounds ----------------------
     const int my = list_mode ? 0 : lane;
     const bool valid = lane < nlanes || list_mode;
     const int64_t i = i0 + my;
-    float a = 0.0f, cw = 0.0f, isd = 0.0f;
+    a = 0.0f;
+    cw = 0.0f;
+    isd = 0.0f;
     if (valid) window_coeffs(C.ref, i, m, s_r + my, a, cw, isd);
-    float lb = 0.0f;
+    lb = 0.0f;
     bool alive = valid && (!list_mode || lane == 0);
     int why = 0;  // 1, 2, 3: pruned by LB_Kim, LB_Keogh EQ, LB_Keogh EC
     if (LB && C.use_lb && alive && !list_mode) {
@@ -306,6 +277,55 @@ __device__ __forceinline__ void process_tile(const TileCtx& C, float* s_r, bool 
             alive = alive && !ab;
         }
     }
+
+    return alive;
+}
+
+// One work item on one warp: a tile of nlanes (<= 32) consecutive windows
+// starting at i0, or (list_mode) the single window i0.  STAGE: copy the
+// windows' points into the warp's shared-memory tile s_r first (one query per
+// launch); otherwise read them from the reference in global memory through L1
+// (a batch, whose query lengths differ from item to item).  Then the lower
+// bounds lane by lane (tile mode), then EAPrunedDTW for every survivor on the
+// whole warp.
+// ECM: where LB_Keogh EC reads the reference envelope: 1 = arrays over the
+// window's own radius; 2 = a sparse table of running maxima / minima (any
+// radius, two reads per bound; windows within the radius of either end of the
+// reference use a slightly wider envelope, which is still a valid bound).
+// JW: 0 = the DP columns' query values held in registers, one window of 32
+// blocks; JW >= 1 = the values streamed from C.zq at every step, JW windows of
+// 32 blocks (fewer registers per thread, more resident warps).
+// TIGHT: upper-bound tightening for the survivors (needs C.cbw and the lower
+// bounds; compiled out otherwise).
+// EL: run the survivors through the narrow-block elastic wavefront
+// (dtw_elastic.cuh; unconstrained, K = kElK, C.zr and C.zq padded as it needs).
+template <int K, int BAND, bool LB, int JW, bool STAGE = true, int ECM = 1, bool TIGHT = false, int COST = 0,
+          bool EL = false, typename CountF>
+__device__ __forceinline__ void process_tile(const TileCtx& C, float* s_r, bool list_mode, int64_t i0,
+                                             int nlanes, CountF count) {
+    const int lane = threadIdx.x & 31;
+    const int m = C.m;
+    const int mp = query_pad(m);
+    const int len = nlanes - 1 + m;
+    if (!EAPDTW_CHECK(C.dbg, i0 >= 0 && i0 + len <= C.ref.n, 21, len)) return;
+    if (STAGE) {
+        // R[i0 .. i0 + nlanes - 1 + m) into the warp's tile.
+        if (!EAPDTW_CHECK(C.dbg, len <= tile_floats(m), 26, len)) return;
+        if ((reinterpret_cast<uintptr_t>(C.ref.R + i0) & 15) == 0 && !list_mode) {
+            const float4* src = reinterpret_cast<const float4*>(C.ref.R + i0);
+            const int nv = len / 4;
+            for (int v = lane; v < nv; v += 32) reinterpret_cast<float4*>(s_r)[v] = __ldg(src + v);
+            for (int j = nv * 4 + lane; j < len; j += 32) s_r[j] = __ldg(C.ref.R + i0 + j);
+        } else {
+            for (int j = lane; j < len; j += 32) s_r[j] = __ldg(C.ref.R + i0 + j);
+        }
+        __syncwarp();
+    } else {
+        s_r = const_cast<float*>(C.ref.R + i0);
+    }
+
+    float a, cw, isd, lb;
+    bool alive = tile_lanes<BAND, LB, ECM, COST>(C, s_r, list_mode, i0, nlanes, count, a, cw, isd, lb);
 
     // ---- EAPrunedDTW on the survivors, one warp per window ----------------
     unsigned mask = __ballot_sync(kFull, alive);

@@ -98,3 +98,38 @@ def test_dominant_shape_audit_counts_bit_exact(kind, m, seed):
         assert {c: gc[c] for c in AUDIT_KEYS} == oc, (tile, gc, oc)
         np.testing.assert_array_equal(gd2.cpu().numpy(), ad)
         np.testing.assert_array_equal(gi2.cpu().numpy(), ai)
+
+
+GROUP_CASES = [
+    # (series, n, m, w, k, seed, tile): the group of warps as the first level
+    # (tile = 512), or as the re-run level after the one-warp levels (tile 0)
+    ("walk", 3_000, 300, 40, 2, 20, 512),     # one warp per group
+    ("ecg", 4_000, 700, 200, 3, 21, 512),     # two warps
+    ("walk", 2_300, 1500, 900, 1, 22, 512),   # three warps
+    ("ecg", 2_800, 2500, 1500, 2, 23, 512),   # five warps
+    ("ecg", 2_800, 2500, 1500, 2, 23, 0),     # the same through the one-warp levels and re-runs
+    ("walk", 4_300, 4096, 4096, 1, 24, 512),  # eight warps, unconstrained
+]
+
+
+@pytest.mark.parametrize("kind,n,m,w,k,seed,tile", GROUP_CASES)
+def test_group_levels_bit_exact(kind, n, m, w, k, seed, tile):
+    """The group wavefront as the first level (its warp 0 runs the
+    lower-bound cascade of each tile, the group the survivors) or as the
+    re-run level: results equal the FP32 emulation's, and under a fixed bound
+    so do the prune, abandon and completion counts, with and without lower
+    bounds."""
+    R, Q = inputs(kind, n, m, seed)
+    ei, ed, _ = O.o7_search(Q, R, w, k)
+    Rd, Qd = dev(R), dev(Q)
+    gi, gd = api.subseq_search(Qd, Rd, w, k, tile=tile)
+    np.testing.assert_array_equal(gd.cpu().numpy(), ed)
+    np.testing.assert_array_equal(gi.cpu().numpy(), ei)
+    ub = float(np.float32(ed[-1] * 1.05))
+    for use_lb in (True, False):
+        ai, ad, oc = O.o7_search(Q, R, w, k, audit_ub=ub, use_lb=use_lb)
+        gi2, gd2, gc = api.subseq_search(Qd, Rd, w, k, audit_ub=ub, no_lb=not use_lb, tile=tile,
+                                         return_counters=True)
+        assert {c: gc[c] for c in AUDIT_KEYS} == oc, (use_lb, gc, oc)
+        np.testing.assert_array_equal(gd2.cpu().numpy(), ad)
+        np.testing.assert_array_equal(gi2.cpu().numpy(), ai)
