@@ -244,6 +244,8 @@ def batched_section(args, dev):
         counts[st] = counts.get(st, 0) + 1
         first.setdefault(st, q)
     picked = sorted(first.values())[:args.batch_queries]
+    if args.batch_strata:   # profiling aid: only these of the sampled strata
+        picked = [picked[int(j)] for j in args.batch_strata.split(",")]
     queries = []
     for q in picked:
         m, w, ecg, k, ratio = mix[q]
@@ -498,6 +500,8 @@ def main():
                     help="query seeds of the step (profiling aid; the benchmark is all four)")
     ap.add_argument("--batch-queries", type=int, default=16,
                     help="strata sampled from the batched mix (one query each, against 8 references); 0 skips it")
+    ap.add_argument("--batch-strata", default="",
+                    help="indices into the sampled strata to run alone (profiling aid; the benchmark runs all)")
     ap.add_argument("--serve-requests", type=int, default=24,
                     help="requests of the saturated and plain serving runs; 0 skips serving")
     ap.add_argument("--serve-poisson-requests", type=int, default=12, help="requests per Poisson rate")
