@@ -304,7 +304,12 @@ int32_t eapdtw_search_batch(eapdtw_ctx* ctx, const eapdtw_item* items, int32_t n
                             int64_t* out_idx, double* out_dist, int64_t* counters, void* stream);
 
 /* eapdtw_set_first_tile - the autotuner's choice of the first level's DP
- * cells per lane (4, 8, 16, 32; 0 = the built-in rule) for items with
+ * cells per lane (4, 8, 16, 32; 1 = the narrow-block elastic wavefront, which
+ * runs queries of 129 to 2048 points that are unconstrained or have a band of
+ * at least 64 and a quarter of lQ, others falling back to the built-in rule;
+ * 0 = the built-in rule: the elastic wavefront where it runs for queries of
+ * up to 1024 points, else the narrowest one-warp K whose window holds the
+ * band or every column) for items with
  * floor(log2 lQ) == log2_m, window ratio floor(10 w / lQ) == ratio_tenths
  * (10 for unconstrained) and band (0 unconstrained, 1 banded).  Any choice
  * gives the same results; only the speed differs. */
@@ -314,8 +319,8 @@ int32_t eapdtw_set_first_tile(eapdtw_ctx* ctx, int32_t log2_m, int32_t ratio_ten
 int32_t eapdtw_get_first_tile(eapdtw_ctx* ctx, int32_t log2_m, int32_t ratio_tenths, int32_t band, int32_t* tile);
 
 /* eapdtw_set_tuning - the autotuner's whole choice for a signature (see
- * eapdtw_set_first_tile): the first level's DP cells per lane (4, 8, 16, 32; 0
- * = the built-in rule) and check_double (1: the warp wavefront checks its
+ * eapdtw_set_first_tile): the first level's DP cells per lane (4, 8, 16, 32, 1
+ * for the elastic wavefront; 0 = the built-in rule) and check_double (1: the warp wavefront checks its
  * borders and the best-so-far bound at twice its built-in interval of 8
  * steps, 16 for the one-window unconstrained levels; 0: the built-in
  * interval).  Both 0 removes the entry.  Any choice gives the same results. */
@@ -331,7 +336,9 @@ int32_t eapdtw_get_tuning(eapdtw_ctx* ctx, int32_t log2_m, int32_t ratio_tenths,
  * eapdtw_set_first_tile) of the n HOST items that has no table entry yet, it
  * times the batched search of one representative item (the one with the
  * longest reference) over a prefix of its reference holding about
- * sample_windows windows, with the built-in K, twice it and half it, each at
+ * sample_windows windows, with the built-in K, twice it and half it (where
+ * the built-in first level is the elastic wavefront: it, the band's one-warp
+ * K and twice that), each at
  * the built-in check interval and at twice it (two runs each, the faster
  * counts, device time of the launch sequence), and enters the fastest pair.
  * *n_tuned (optional) receives the number of signatures entered.  Blocking;

@@ -46,6 +46,7 @@ SPLIT_UNITS = {
                               for (lb, c) in ((0, 0), (1, 0), (0, 1)) for b in (0, 1, 2)],
     "batch_wide.cu": [[]] + [[f"-DEAPDTW_UNIT_LEVEL={lv}", f"-DEAPDTW_UNIT_BAND={b}"] for lv in (4, 5) for b in (0, 1, 2)],
     "pair_kernel.cu": [[], ["-DEAPDTW_UNIT_PAIR_WIDE"]],
+    "search_elastic.cu": [[], ["-DEAPDTW_UNIT_EBAND=0"], ["-DEAPDTW_UNIT_EBAND=1"]],
     "search_k.cu": [[f"-DEAPDTW_UNIT_K={k}"] for k in (32, 16, 8, 4)],
     "batch_k.cu": [[f"-DEAPDTW_UNIT_K={k}"] for k in (32, 16, 8, 4)],
 }

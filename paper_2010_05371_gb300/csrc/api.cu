@@ -280,7 +280,7 @@ int32_t search_impl(Scratch& S, const float* Q, int64_t lQ, const float* R, int6
         if (plan.wide[lev]) {
             CK(launch_search_wide(plan.band[lev], lb, la, search_blocks_wide(plan.band[lev], lb, m, cost), st, cost));
         } else if (plan.elastic[lev]) {
-            CK(launch_search_elastic(lb, la, search_blocks_elastic(lb, m, cost), st, cost));
+            CK(launch_search_elastic(lb, plan.band[lev], la, search_blocks_elastic(lb, plan.band[lev], m, cost), st, cost));
         } else if (lev == 0 && probe) {
             // the probe (sampled windows, single-window mode, overflows only
             // counted), then the first level at the planned or the next width:

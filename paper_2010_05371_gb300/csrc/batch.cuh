@@ -22,11 +22,17 @@
 
 namespace eapdtw {
 
-// Levels: K = 4, 8, 16, 32 with one window of 32 blocks, then K = 32 with the
-// columns streamed from shared memory and two windows (queries up to 2048
-// points) or four windows (longer queries).
+// Levels: K = 4, 8, 16, 32 with one window of 32 blocks, then the group
+// wavefront with groups of 4 warps (queries up to 2048 points) or 8 (longer
+// queries).  Before them, for unconstrained and wide-band items of up to 2048
+// points, the elastic first level (launched before level 0).
 constexpr int kBatchLevels = 6;
-constexpr int kBatchClasses = 12;    // first levels 0..3 x band modes 0..2
+constexpr int kElLevel = 6;          // the elastic first level
+constexpr int kElClasses = 4;        // band mode 0 / 1 x queries up to 1024 / 2048 points
+constexpr int kElClass0 = 12;
+constexpr int kElMaxM = 2048;
+constexpr int kTileElastic = 1;      // the tuning table's first-level tile for the elastic level
+constexpr int kBatchClasses = 12 + kElClasses;   // tile classes: first levels 0..3 x band modes 0..2, then the elastic ones
 constexpr int kSeedClasses = 9;      // seed passes at levels 3, 4, 5 x band modes
 constexpr int kRerunBuffers = 3;     // re-run lists of level L live in buffer L % 3
 constexpr int kAllClasses = kBatchClasses + kSeedClasses;
@@ -62,8 +68,9 @@ struct BatchItem {
     int seed_ns;         // sampled windows (0: no seed)
     int check2;          // 1: the wavefront checks at twice its built-in interval (autotuner)
     int level0;          // first level
-    int next_level[kBatchLevels];  // level that re-runs windows overflowing level L (-1: none)
-    int next_band[kBatchLevels];   // its band mode
+    int next_level[kBatchLevels + 1];  // level that re-runs windows overflowing level L (-1: none;
+                                       // index kElLevel: the elastic first level)
+    int next_band[kBatchLevels + 1];   // its band mode
     const float* eu;     // sparse-table level of the reference for LB_Keogh EC (see TileCtx)
     const float* el;
     int ec_w, ec_d;

@@ -19,7 +19,9 @@ __host__ __device__ constexpr int batch_group_warps(int level) { return level ==
 template <int BAND, int GW>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32, EAPDTW_MINB_GROUP) batch_group_kernel(const BatchLaunch L) {
     constexpr int kGroups = kWarpsPerBlock / GW;
+    constexpr int kTile = GW * kGrpCols;   // the longest window a group runs
     __shared__ GroupSync s_gs[kGroups];
+    __shared__ __align__(16) float s_win[kGroups][kTile];   // each group's window, staged once per candidate
     __shared__ unsigned long long s_cnt[kNumCounters];
     if (threadIdx.x < kNumCounters) s_cnt[threadIdx.x] = 0;
     __syncthreads();
@@ -70,11 +72,17 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, EAPDTW_MINB_GROUP) batch_
         }
         const BatchItem& it = L.D.items[item];
         const int ge = group_warps(it.m);
-        if (run && g < ge && ge <= GW) {
+        const bool go = run && ge <= GW && it.m <= kTile;
+        if (go) {   // the window's points into the group's tile, by all its warps
+            const float* src = it.ref.R + i0;
+            for (int j = g * 32 + lane; j < it.m; j += GW * 32) s_win[gi][j] = __ldg(src + j);
+        }
+        group_bar(gi, GW);
+        if (go && g < ge) {
             const long long c0 = clock64();
             const BestSoFar bsf{L.D.slots + static_cast<int64_t>(it.state) * kBatchSlots, L.D.ub_seed + it.state,
                                 it.k, 0, 0.0f};
-            const float* x = it.ref.R + i0;
+            const float* x = s_win[gi];
             float a = 0.0f, cw = 0.0f, isd = 0.0f;
             if (lane == 0) window_coeffs(it.ref, i0, it.m, x, a, cw, isd);
             a = __shfl_sync(kFull, a, 0);

@@ -19,6 +19,7 @@
 #include "ctx_internal.h"
 #include "eapdtw.h"
 #include "kernels.h"
+#include "plan.h"
 
 namespace eapdtw {
 
@@ -144,14 +145,33 @@ cudaError_t enqueue_sequence(Arena& a, cudaStream_t s) {
         e = launch_batch(L.level, L.band, L, batch_blocks(L.level, L.band), s);
         if (e != cudaSuccess) return e;
     }
+    // The re-run lists of levels 1, 2 and 3 (buffers 1, 2, 0) start empty: the
+    // elastic first level and levels 0..2 fill them.  Levels 4 and 5 reuse
+    // buffers 1 and 2 once levels 1 and 2 have read them.
+    e = cudaMemsetAsync(rrc, 0, sizeof(int) * 3 * kRerunBuffers, s);
+    if (e != cudaSuccess) return e;
+    for (int ec = 0; ec < kElClasses; ++ec) {
+        BatchLaunch L{};
+        L.D = D;
+        L.level = kElLevel;
+        L.band = ec & 1;
+        L.cls = kElClass0 + ec;
+        L.scls = -1;
+        L.rr_in = nullptr;
+        L.rr_in_count = rrc;
+        L.rr = a.rr;
+        L.rr_count = rrc;
+        L.rr_cap = a.rr_cap;
+        L.work = a.work() + kElWork0 + ec;
+        L.counters = a.counters();
+        L.lb_scale = kBatchLbScale;
+        e = launch_batch_elastic(ec, L, batch_blocks_el(ec), s);
+        if (e != cudaSuccess) return e;
+    }
     for (int level = 0; level < kBatchLevels; ++level) {
-        // the lists this level fills start empty: level + 1's, and level 5's from level 3
-        if (level <= 3) {
-            e = cudaMemsetAsync(rrc + 3 * ((level + 1) % kRerunBuffers), 0, sizeof(int) * 3, s);
-            if (e != cudaSuccess) return e;
-        }
-        if (level == 3) {
-            e = cudaMemsetAsync(rrc + 3 * (5 % kRerunBuffers), 0, sizeof(int) * 3, s);
+        if (level == 3) {   // the lists of levels 4 and 5
+            e = cudaMemsetAsync(rrc + 3 * (4 % kRerunBuffers), 0, sizeof(int) * 3, s);
+            if (e == cudaSuccess) e = cudaMemsetAsync(rrc + 3 * (5 % kRerunBuffers), 0, sizeof(int) * 3, s);
             if (e != cudaSuccess) return e;
         }
         const int bin = level % kRerunBuffers;
@@ -183,6 +203,7 @@ int32_t ensure_graph(Arena& a) {
     // occupancy queries before the capture (they are not stream work)
     for (int level = 0; level < kBatchLevels; ++level)
         for (int band = 0; band < 3; ++band) batch_blocks(level, band);
+    for (int ec = 0; ec < kElClasses; ++ec) batch_blocks_el(ec);
     if (!a.cap_stream && cudaStreamCreateWithFlags(&a.cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
         cudaGetLastError();
         return EAPDTW_ERR_CUDA;
@@ -277,25 +298,50 @@ std::tuple<int, int, int> signature(int m, int w) {
     return std::make_tuple(lg, tenth, unc ? 0 : 1);
 }
 
-// First level (block width 4 << level) of a (query length, window) pair: the
-// narrowest K whose window of 32 blocks covers the band with margin, 8 (or 4
-// for short queries) when unconstrained, unless the autotuner chose otherwise.
-int first_level(const eapdtw_ctx* c, int m, int w) {
+// One-warp level (block width 4 << level) of a (query length, window) pair:
+// the narrowest K whose window of 32 blocks covers the band with margin or
+// every column, 8 (or 4 for short queries) when unconstrained.
+int rule_level(int m, int w) {
     const bool unconstrained = w >= m - 1;
     int K = 32;
     if (!unconstrained) {
         for (int k = 4; k <= 32; k *= 2)
-            if ((2 * w + k) / (k + 1) + 3 <= 32) { K = k; break; }
+            if ((2 * w + k) / (k + 1) + 3 <= 32 || 32 * k >= m) { K = k; break; }
     } else {
         K = 8;
         for (int k = 4; k <= 8; k *= 2)
             if (32 * k >= m) { K = k; break; }
     }
-    auto it = c->tuned.find(signature(m, w));
-    if (it != c->tuned.end() && it->second.first) K = it->second.first;
     int level = 0;
     while ((4 << level) < K) ++level;
     return level;
+}
+
+// Whether the elastic wavefront can be the first level: queries of 129 to
+// kElMaxM points, unconstrained or with a band as wide as the one-query
+// search's plan asks (plan.h).
+bool elastic_ok(int m, int w) {
+    if (m <= 128 || m > kElMaxM) return false;
+    return w >= m - 1 || (w >= kElBandMinW && 4 * w >= kElBandMinQuarters * m);
+}
+
+// First level of a pair: the autotuner's choice (tile 1: the elastic
+// wavefront; 4..32: that one-warp level), else the elastic wavefront where it
+// can run for queries of up to 1024 points, else rule_level.  Longer queries
+// start on one warp: measured on the batched mix, their wide bands come with
+// wide live regions (long ECG-like queries against random walks), most
+// candidates are handed over, and the elastic pass made those items 3-6%
+// slower (the autotuner may still choose it).
+int first_level(const eapdtw_ctx* c, int m, int w) {
+    auto it = c->tuned.find(signature(m, w));
+    if (it != c->tuned.end() && it->second.first) {
+        const int K = it->second.first;
+        if (K == kTileElastic) return elastic_ok(m, w) ? kElLevel : rule_level(m, w);
+        int level = 0;
+        while ((4 << level) < K) ++level;
+        return level;
+    }
+    return (m <= 1024 && elastic_ok(m, w)) ? kElLevel : rule_level(m, w);
 }
 int check_choice(const eapdtw_ctx* c, int m, int w) {
     auto it = c->tuned.find(signature(m, w));
@@ -329,6 +375,11 @@ void plan_item(const eapdtw_ctx* c, const RefEntry& r, int64_t n_used, int m, in
         b.next_level[lv] = nx;
         b.next_band[lv] = nx >= 0 ? band_mode(nx, w, unc) : -1;
     }
+    // the elastic level hands its overflows to K = 16 (unconstrained: its
+    // windows hold 384 columns) or to the band's one-warp level
+    const int enx = unc ? 2 : rule_level(m, w);
+    b.next_level[kElLevel] = enx;
+    b.next_band[kElLevel] = band_mode(enx, w, unc);
     const int er = std::min(w, m - 1);
     const int ep = env_level(er);
     b.ec_w = er;
@@ -336,7 +387,8 @@ void plan_item(const eapdtw_ctx* c, const RefEntry& r, int64_t n_used, int m, in
     b.eu = no_lb ? nullptr : r.emax[ep];
     b.el = no_lb ? nullptr : r.emin[ep];
     b.fresh = 1;
-    out.cls = b.level0 * 3 + band_mode(b.level0, w, unc);
+    out.cls = b.level0 == kElLevel ? kElClass0 + 2 * (m > 1024 ? 1 : 0) + (unc ? 0 : 1)
+                                   : b.level0 * 3 + band_mode(b.level0, w, unc);
     out.scls = kBatchClasses + 3 * (last - 3) + band_mode(last, w, unc);
     out.tiles = (b.nwin + 31) / 32;
 }
@@ -608,6 +660,8 @@ cudaError_t batch_attributes_k8();
 cudaError_t batch_attributes_k16();
 cudaError_t batch_attributes_k32();
 cudaError_t batch_attributes_wide();
+int batch_blocks_elastic(int e);
+cudaError_t batch_attributes_elastic();
 
 cudaError_t launch_batch(int level, int band, const BatchLaunch& args, int blocks, cudaStream_t s) {
     switch (level) {
@@ -645,7 +699,19 @@ cudaError_t batch_attributes() {
     if (e == cudaSuccess) e = batch_attributes_k16();
     if (e == cudaSuccess) e = batch_attributes_k32();
     if (e == cudaSuccess) e = batch_attributes_wide();
+    if (e == cudaSuccess) e = batch_attributes_elastic();
     return e;
+}
+
+int batch_blocks_el(int ec) {
+    static std::mutex mu;
+    static int cache[64][kElClasses] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lk(mu);
+    int& v = cache[dev & 63][ec];
+    if (v == 0) v = batch_blocks_elastic(ec);
+    return v;
 }
 
 }  // namespace eapdtw
@@ -779,7 +845,8 @@ int32_t eapdtw_ctx_info(eapdtw_ctx* c, int64_t* out, int32_t nout) {
 int32_t eapdtw_set_first_tile(eapdtw_ctx* c, int32_t log2_m, int32_t ratio_tenths, int32_t band, int32_t tile) {
     if (!c || log2_m < 0 || log2_m > 12 || ratio_tenths < 0 || ratio_tenths > 10 || band < 0 || band > 1)
         return EAPDTW_ERR_INVALID_ARG;
-    if (tile != 0 && tile != 4 && tile != 8 && tile != 16 && tile != 32) return EAPDTW_ERR_INVALID_ARG;
+    if (tile != 0 && tile != kTileElastic && tile != 4 && tile != 8 && tile != 16 && tile != 32)
+        return EAPDTW_ERR_INVALID_ARG;
     std::lock_guard<std::mutex> lk(c->mu);
     const auto key = std::make_tuple(static_cast<int>(log2_m), static_cast<int>(ratio_tenths), static_cast<int>(band));
     auto f = c->tuned.find(key);
@@ -801,7 +868,8 @@ int32_t eapdtw_set_tuning(eapdtw_ctx* c, int32_t log2_m, int32_t ratio_tenths, i
                           int32_t check_double) {
     if (!c || log2_m < 0 || log2_m > 12 || ratio_tenths < 0 || ratio_tenths > 10 || band < 0 || band > 1)
         return EAPDTW_ERR_INVALID_ARG;
-    if ((tile != 0 && tile != 4 && tile != 8 && tile != 16 && tile != 32) || check_double < 0 || check_double > 1)
+    if ((tile != 0 && tile != kTileElastic && tile != 4 && tile != 8 && tile != 16 && tile != 32) || check_double < 0 ||
+        check_double > 1)
         return EAPDTW_ERR_INVALID_ARG;
     std::lock_guard<std::mutex> lk(c->mu);
     const auto key = std::make_tuple(static_cast<int>(log2_m), static_cast<int>(ratio_tenths), static_cast<int>(band));
@@ -874,13 +942,27 @@ int32_t eapdtw_autotune(eapdtw_ctx* c, const eapdtw_item* items, int32_t n, int6
         const int m = static_cast<int>(it.lQ);
         const int w = static_cast<int>(it.w < m ? it.w : m);
         c->tuned.erase(kv.first);
-        const int base = 4 << first_level(c, m, w);
-        const int cand[3] = {base, base * 2, base / 2};
+        // candidates: the built-in first level and its neighbours (the
+        // elastic level, where it can run, against the band's one-warp K and
+        // twice that)
+        const int lv0 = first_level(c, m, w);
+        int cand[3];
+        if (lv0 == kElLevel) {
+            const int kr = 4 << rule_level(m, w);
+            cand[0] = kTileElastic;
+            cand[1] = kr;
+            cand[2] = kr * 2;
+        } else {
+            const int base = 4 << lv0;
+            cand[0] = base;
+            cand[1] = base * 2;
+            cand[2] = base / 2;
+        }
         float best_ms = INFINITY;
-        std::pair<int, int> best(base, 0);
+        std::pair<int, int> best(cand[0], 0);
         for (int chk = 0; chk < 2 && rc == EAPDTW_OK; ++chk) {
             for (int K : cand) {
-                if (K < 4 || K > 32) continue;
+                if (K != kTileElastic && (K < 4 || K > 32)) continue;
                 c->tuned[kv.first] = std::make_pair(K, chk);
                 float ms = 0.0f, ms2 = 0.0f;
                 rc = run_batch(c, &it, 1, it.k, d_idx, d_dist, nullptr, stream, &len, &ms);   // warm-up

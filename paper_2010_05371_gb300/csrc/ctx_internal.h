@@ -17,7 +17,8 @@ namespace eapdtw {
 
 constexpr int kEnvLevels = 13;   // running extrema over 2^p points, p = 0..12 (radius <= 4095)
 constexpr float kBatchLbScale = 1.0001f;   // prune iff lb > ub * scale (as subseq_search)
-constexpr int kNumWork = kBatchLevels * 3 + kSeedClasses;
+constexpr int kNumWork = kBatchLevels * 3 + kSeedClasses + kElClasses;
+constexpr int kElWork0 = kBatchLevels * 3 + kSeedClasses;   // work counters of the elastic classes
 
 struct RefEntry {
     bool live = false;

@@ -83,8 +83,8 @@ constexpr int kElPadCols = 32 * kElJ * kElK;
 
 // Floats of the per-warp row buffer (rows start at offset kElPadRows) and of
 // the query buffer (NaN past the last column) for queries of m points.
-__host__ __device__ inline int elastic_row_floats(int m) { return (2 * kElPadRows + m + kElR + 3) / 4 * 4; }
-__host__ __device__ inline int elastic_col_floats(int m) { return (m + kElPadCols + 3) / 4 * 4; }
+__host__ __device__ constexpr int elastic_row_floats(int m) { return (2 * kElPadRows + m + kElR + 3) / 4 * 4; }
+__host__ __device__ constexpr int elastic_col_floats(int m) { return (m + kElPadCols + 3) / 4 * 4; }
 // Cells one busy lane-step computes.
 constexpr int kElCellsPerStep = kElK * kElR;
 
@@ -98,8 +98,7 @@ static_assert(kElFillRows >= 32 && kElFillRows % 32 == 0, "whole warps of rows")
 
 // zr: minus row r (1-based), -z_r, at zr[r - 1] (so that d = q + (-z) is one
 // add, packed or not), NaN at zr[-kElPadRows .. -1] and
-// zr[nr .. nr + kElPadRows + 2); zq: column c at zq[c - 1], NaN from zq[nc]
-// through zq[nc + kElPadCols - 1], 16-byte aligned.  All 32 lanes call it
+// zr[nr .. nr + kElPadRows + 2); zq: column c at zq[c - 1] (c <= nc).  All 32 lanes call it
 // with identical arguments.  Returns busy = lane-steps executed by the
 // active windows (started or not).
 //
@@ -113,9 +112,22 @@ static_assert(kElFillRows >= 32 && kElFillRows % 32 == 0, "whole warps of rows")
 // active windows (1..J), so that a step computes only the active windows and
 // inactive ones hold no live state: a window's state is reset when it is
 // switched on.
-template <int J, int COST, typename FillF>
+//
+// BANDED: the window |r - c| <= w (Section 2.1) without forcing any cell: the
+// recurrence runs unconstrained, and at every check the candidate is handed to
+// the banded levels (status 1, as an overflow) unless no alive cell of the
+// next kElCE steps can lie outside the band.  Block b at step s holds cells
+// with c - r <= 6 b - 2 s + 5 and r - c <= 2 s - 6 b - 1; the highest alive
+// block grows by at most one per step and no block left of the retirable
+// leading ones revives, so with H the highest alive block and L the first
+// non-retirable one at check t, the next steps keep c - r <= 6 H - 2 t +
+// 4 kElCE + 5 and r - c <= 2 (t + kElCE) - 6 L - 1.  While both stay within w,
+// every alive cell's optimal path lies in the band, so its value is the banded
+// DP's (the same operations on the same inputs; dead out-of-band values lose
+// every min to the alive ones), and the result is the banded EAPrunedDTW's.
+template <int J, int COST, bool BANDED, typename FillF>
 __device__ __forceinline__ DtwOut dtw_elastic(const float* __restrict__ zr, const float* __restrict__ zq, int nr,
-                                              int nc, const BestSoFar bsf, float ub, FillF fill) {
+                                              int nc, const BestSoFar bsf, float ub, int w, FillF fill) {
     constexpr int K = kElK;
     constexpr int CE = kElCE;
     const int lane = threadIdx.x & 31;
@@ -135,8 +147,20 @@ __device__ __forceinline__ DtwOut dtw_elastic(const float* __restrict__ zr, cons
         lo1[j] = INF;
         dg[j] = INF;
     };
+    // columns past nc are NaN: read from the array only below nc (it may hold
+    // just nc values, in shared or global memory)
     auto load_q = [&](int j) {
-        const float4 v = *reinterpret_cast<const float4*>(zq + (B0 + 32 * j + lane) * K);
+        const int c0 = (B0 + 32 * j + lane) * K;
+        float4 v;
+        if (c0 + K <= nc && (reinterpret_cast<uintptr_t>(zq + c0) & 15) == 0) {
+            v = *reinterpret_cast<const float4*>(zq + c0);
+        } else {
+            const float nan = f_nan();
+            v.x = c0 < nc ? zq[c0] : nan;
+            v.y = c0 + 1 < nc ? zq[c0 + 1] : nan;
+            v.z = c0 + 2 < nc ? zq[c0 + 2] : nan;
+            v.w = c0 + 3 < nc ? zq[c0 + 3] : nan;
+        }
         q[j][0] = v.x; q[j][1] = v.y; q[j][2] = v.z; q[j][3] = v.w;
         if (kElPaired) {
             qp[kElPaired ? j : 0][0] = make_float2(v.y, v.x);
@@ -185,6 +209,10 @@ __device__ __forceinline__ DtwOut dtw_elastic(const float* __restrict__ zr, cons
     const bool last_first = (nr & 1) != 0;    // row nr is the first of its step's two rows
     DtwOut out{INF, 0, 0, 0};
     int busy = 0;   // window-steps (the same on every lane)
+    if (BANDED && w < 4 * CE) {   // the first steps, before any check, need c - r <= 4 CE - 1
+        out.status = 1;
+        return out;
+    }
 
     // nz = -z: d = q + nz = q - z exactly
     auto cost = [&](float qv, float nz, float mn) -> float {
@@ -281,6 +309,8 @@ __device__ __forceinline__ DtwOut dtw_elastic(const float* __restrict__ zr, cons
         const unsigned cond = db[0] & ((da[0] << 1) | 1u);   // retirable leading blocks of window 0
         if (all_dead || (JA == 1 && cond == kFull)) return 1;
         const int d = (cond == kFull) ? 32 : (__ffs(~cond) - 1);
+        if (BANDED && (6 * (B0 + hi) - 2 * t + 4 * CE + 5 > w || 2 * (t + CE) - 6 * (B0 + d) - 1 > w))
+            return 2;   // an alive cell may leave the band: the banded levels re-run it
         // windows needed without and with the slide (an alive block needs
         // CE + 1 blocks after it), capped by the window holding the last column
         auto need = [&](int sh) {

@@ -43,10 +43,10 @@ int search_blocks(int K, int band, bool lb, int m, bool tight = false, int cost 
 cudaError_t launch_search_wide(int band, bool lb, const SearchArgs& args, int blocks, cudaStream_t s, int cost = 0);
 int search_blocks_wide(int band, bool lb, int m, int cost = 0);
 
-// The unconstrained first level with the narrow-block elastic wavefront
-// (search_elastic_kernel; tile mode only).
-cudaError_t launch_search_elastic(bool lb, const SearchArgs& args, int blocks, cudaStream_t s, int cost = 0);
-int search_blocks_elastic(bool lb, int m, int cost = 0);
+// The first level with the narrow-block elastic wavefront
+// (search_elastic_kernel; tile mode only): band 0 unconstrained, 1 banded.
+cudaError_t launch_search_elastic(bool lb, int band, const SearchArgs& args, int blocks, cudaStream_t s, int cost = 0);
+int search_blocks_elastic(bool lb, int band, int m, int cost = 0);
 
 // eap_dtw single pair: one warp; wide selects the four-window level.
 cudaError_t launch_pair(int K, int band, bool wide, const float* rows, int nr, const float* cols, int nc,
@@ -70,5 +70,8 @@ cudaError_t launch_batch_finalize(const BatchDev& D, cudaStream_t s);
 cudaError_t launch_batch(int level, int band, const BatchLaunch& args, int blocks, cudaStream_t s);
 int batch_blocks(int level, int band);
 cudaError_t batch_attributes();
+// The elastic first level of the batch (batch_elastic.cu): class kElClass0 + ec.
+cudaError_t launch_batch_elastic(int ec, const BatchLaunch& args, int blocks, cudaStream_t s);
+int batch_blocks_el(int ec);
 
 }  // namespace eapdtw

@@ -173,7 +173,7 @@ extern "C" int32_t subseq_search_noalloc(const float* Q, int64_t lQ, const float
         if (plan.wide[lev]) {
             CKN(launch_search_wide(plan.band[lev], lb, la, search_blocks_wide(plan.band[lev], lb, m), st));
         } else if (plan.elastic[lev]) {
-            CKN(launch_search_elastic(lb, la, search_blocks_elastic(lb, m), st));
+            CKN(launch_search_elastic(lb, plan.band[lev], la, search_blocks_elastic(lb, plan.band[lev], m), st));
         } else {
             CKN(launch_search(plan.K[lev], plan.band[lev], lb, la, search_blocks(plan.K[lev], plan.band[lev], lb, m), st));
         }

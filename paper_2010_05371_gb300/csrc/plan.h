@@ -25,13 +25,24 @@ struct Plan {
 
 // Tile hint that makes the first level a group of warps (any query length).
 constexpr int kGroupTileHint = 512;
+// Bands that start on the elastic wavefront: w >= kElBandMinW and w >= nc x
+// kElBandMinQuarters / 4 (compile-time knobs for tuning experiments).
+#ifndef EAPDTW_ELASTIC_BAND_MIN_W
+#define EAPDTW_ELASTIC_BAND_MIN_W 64
+#endif
+#ifndef EAPDTW_ELASTIC_BAND_MIN_QUARTERS
+#define EAPDTW_ELASTIC_BAND_MIN_QUARTERS 1
+#endif
+constexpr int kElBandMinW = EAPDTW_ELASTIC_BAND_MIN_W;
+constexpr int kElBandMinQuarters = EAPDTW_ELASTIC_BAND_MIN_QUARTERS;
 
 // nr, nc: rows and columns of the DP (window and query lengths); w: the window
 // (w >= max(nr, nc) - 1 is unconstrained); tile_hint: 4, 8, 16 or 32 fixes the
 // first level's K, kGroupTileHint makes it a group of warps, 0 chooses.
-// search_levels: the first level may be the elastic wavefront (unconstrained)
-// or, on request, a group of warps; neither implements upper-bound tightening,
-// and the pair kernel has neither.
+// search_levels: the first level may be the elastic wavefront (unconstrained,
+// or a band of at least kElBandMinW and a quarter of the query) or, on
+// request, a group of warps; neither implements upper-bound tightening, and
+// the pair kernel has neither.
 inline Plan plan_levels(int64_t nr, int64_t nc, int64_t w, int tile_hint, bool search_levels = true) {
     const int64_t lmax = nr > nc ? nr : nc;
     const bool unconstrained = w >= lmax - 1;
@@ -48,9 +59,21 @@ inline Plan plan_levels(int64_t nr, int64_t nc, int64_t w, int tile_hint, bool s
         p.nlev = 1;
         return p;
     } else if (!unconstrained) {
-        // blocks spanned by the band across the pipelined rows, plus margin
+        // blocks spanned by the band across the pipelined rows, plus margin;
+        // no wider than needed for one window to hold every column (then
+        // nothing can overflow it)
         for (int K = 4; K <= 32; K *= 2)
-            if ((2 * w + K) / (K + 1) + 3 <= 32) { k0 = K; break; }
+            if ((2 * w + K) / (K + 1) + 3 <= 32 || 32 * K >= nc) { k0 = K; break; }
+        // A wide band: the elastic wavefront first, handing the candidates
+        // whose live region nears the band's edges (or outgrows its windows)
+        // to the banded levels below.
+        if (search_levels && nc > 32 * 4 && w >= kElBandMinW && 4 * w >= kElBandMinQuarters * nc) {
+            p.K[0] = kElK;
+            p.band[0] = 1;
+            p.wide[0] = false;
+            p.elastic[0] = true;
+            p.nlev = 1;
+        }
         // A band that fits no warp's window still starts with one warp at
         // K = 32: measured on GB300 a group of warps as the first level was
         // slower (its warps wait on one another while the live region is

@@ -354,7 +354,7 @@ __device__ __forceinline__ void process_tile(const TileCtx& C, float* s_r, bool 
         if (TIGHT) tightening_terms(C, s_r + off, a_s, cw_s, isd_s);
         DtwOut o;
         if constexpr (EL) {
-            static_assert(BAND == 0 && !TIGHT, "the elastic wavefront is unconstrained, without tightening");
+            static_assert(BAND <= 1 && !TIGHT, "the elastic wavefront: unconstrained or banded, without tightening");
             // the window's z-normalised rows, negated, into the warp's buffer
             // as the wavefront reaches them (the same znorm1 values the other
             // wavefront computes row by row)
@@ -364,7 +364,7 @@ __device__ __forceinline__ void process_tile(const TileCtx& C, float* s_r, bool 
                 for (int i = r0 + lane; i < r1; i += 32) zr[i] = -znorm1(xw[i], a_s, cw_s, isd_s);
                 __syncwarp();
             };
-            o = dtw_elastic<kElJ, COST>(C.zr, C.zq, m, m, C.bsf, ub, fill);
+            o = dtw_elastic<kElJ, COST, (BAND != 0)>(C.zr, C.zq, m, m, C.bsf, ub, C.w, fill);
             __syncwarp();   // every lane is done with the rows before the next survivor's
         } else {
             constexpr int kJ = JW > 0 ? JW : dtw_windows(K, BAND);
@@ -508,9 +508,10 @@ search_kernel(const SearchArgs A) {
 }
 
 // ---------------------------------------------------------------------------
-// The unconstrained first level with the narrow-block elastic wavefront
-// (dtw_elastic.cuh).  Tile mode only (the re-runs of overflowed windows use
-// search_kernel's list mode).  Windows are read through L1 from the
+// The first level with the narrow-block elastic wavefront (dtw_elastic.cuh):
+// unconstrained (BAND = 0), or banded (BAND = 1: candidates whose live region
+// may leave the band go to the banded levels).  Tile mode only (the re-runs
+// of overflowed windows use search_kernel's list mode).  Windows are read through L1 from the
 // reference (no staged tile); shared memory holds the query, NaN-padded past
 // its last column, the lower-bound arrays when LB, and one row buffer per warp
 // with its NaN pads.
@@ -533,7 +534,7 @@ __host__ inline size_t elastic_smem_bytes(int m, bool lb) {
 #ifndef EAPDTW_MINB_ELASTIC
 #define EAPDTW_MINB_ELASTIC 3
 #endif
-template <bool LB, int COST>
+template <bool LB, int BAND, int COST>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32, EAPDTW_MINB_ELASTIC) search_elastic_kernel(const SearchArgs A) {
     extern __shared__ __align__(16) float smem[];
     const int m = A.q.m;
@@ -605,7 +606,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, EAPDTW_MINB_ELASTIC) sear
         item = __shfl_sync(kFull, item, 0);
         if (item >= nitems) break;
         const int64_t i0 = (tile_lo + item) * 32;
-        process_tile<kElK, 0, LB, 0, false, 1, false, COST, true>(
+        process_tile<kElK, BAND, LB, 0, false, 1, false, COST, true>(
             C, nullptr, false, i0, static_cast<int>(A.nw - i0 < 32 ? A.nw - i0 : 32), count);
     }
 

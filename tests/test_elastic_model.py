@@ -43,7 +43,7 @@ def _ffs(x):
     return (x & -x).bit_length() if x else 0
 
 
-def emu(rows, cols, ub, J=3, ub_sched=None, CE=CE):
+def emu(rows, cols, ub, J=3, ub_sched=None, CE=CE, w=None):
     nr, nc = len(rows), len(cols)
     padr = R * 32 * J
     padc = 32 * J * K
@@ -136,7 +136,18 @@ def emu(rows, cols, ub, J=3, ub_sched=None, CE=CE):
             mn = fmin3(fmin3(b0, b1, b2), b3, a3)
             if which == 1: bma[j] = mn
             if which == 2: bmb[j] = mn
+            if w is not None:
+                # banded: every alive cell computed lies in the band
+                b = st["B0"] + 32 * j + lanes
+                for row_off, vals in ((1, (a0, a1, a2, a3)), (2, (b0, b1, b2, b3))):
+                    r = 2 * (s - 1 - b) + row_off
+                    for k, v in enumerate(vals):
+                        c = 4 * b + 1 + k
+                        bad = (v <= ub) & (r >= 1) & (r <= nr) & (c <= nc) & (np.abs(r - c) > w)
+                        assert not bad.any(), ("alive cell outside the band", s, int(np.argmax(bad)))
 
+    if w is not None and w < 4 * CE:
+        return ("ovf", 0), None
     t = 0
     while True:
         jact = st["jact"]
@@ -162,6 +173,8 @@ def emu(rows, cols, ub, J=3, ub_sched=None, CE=CE):
                 return ("abandon", t), None
             d = 32 if cond == FULL else _ffs(~cond & FULL) - 1
             B0 = st["B0"]
+            if w is not None and (6 * (B0 + hi) - 2 * t + 4 * CE + 5 > w or 2 * (t + CE) - 6 * (B0 + d) - 1 > w):
+                return ("ovf", t), None   # an alive cell may leave the band: the banded levels re-run it
 
             def need(shift):
                 nd = int((hi - shift + CE + 1) / 32) + 1   # C integer division truncates toward zero
@@ -316,3 +329,58 @@ def test_benchmark_shape_near_the_nearest_neighbour():
         outcomes[s] = outcomes.get(s, 0) + 1
         _check(s, val, d, ub, ub, i)
     assert outcomes.get("done", 0) >= 4 and outcomes.get("abandon", 0) >= 8, outcomes
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_banded_handover_keeps_alive_cells_in_the_band(seed):
+    """The banded elastic wavefront: unconstrained cells, and a hand-over to the
+    banded levels when an alive cell could leave |r - c| <= w before the next
+    check.  Every alive cell the model computes lies in the band (asserted
+    cell by cell), a finished value equals the banded DTW, an abandoned
+    candidate's banded DTW exceeds ub, and both outcomes and hand-overs occur."""
+    rng = np.random.default_rng(40 + seed)
+    R = synth.random_walk(60_000, 80 + seed)
+    E = synth.ecg_like(60_000, 20 + seed)
+    counts = {}
+    for trial in range(8):
+        m = int(rng.choice([150, 300, 512]))
+        w = int(rng.choice([40, 64, m // 4, m // 2, int(0.9 * m)]))
+        src = E if trial % 2 else R
+        q = synth.random_walk(m, 500 + 10 * seed + trial)
+        zq = O.znorm(q).astype(np.float32)
+        if trial % 4 < 2:   # a near copy of the query: a small DTW, a narrow live region
+            zr = O.znorm(q + rng.normal(0.0, 0.5, m)).astype(np.float32)
+        else:
+            i = int(rng.integers(0, len(src) - m))
+            zr = O.znorm(src[i:i + m]).astype(np.float32)
+        d = O.dtw(zr.astype(np.float64), zq.astype(np.float64), w)
+        for f in (np.inf, 1.5, 1.0005, 0.8):
+            ub = d * f if np.isfinite(f) else np.inf
+            (s, _), val = emu(zr, zq, ub, 3, None, CE, w)
+            counts[s] = counts.get(s, 0) + 1
+            _check(s, val, d, ub, ub, (m, w, f))
+    assert counts.get("done", 0) > 0 and counts.get("abandon", 0) > 0 and counts.get("ovf", 0) > 0, counts
+
+
+@pytest.mark.parametrize("lead", [1, -1])
+def test_banded_handover_with_paths_along_a_band_edge(lead):
+    """Candidates that lead or lag the query by about the band's width: the
+    warping path runs along one edge of the band (r - c near +w or -w), so the
+    hand-over is decided by that edge's rule; every alive cell stays in the
+    band and the outcomes agree with the banded DTW."""
+    rng = np.random.default_rng(7 if lead > 0 else 8)
+    counts = {}
+    for m, w in ((300, 80), (400, 160), (512, 200)):
+        x = synth.random_walk(m + 400, 900 + m)
+        for shift in (20, w // 2, w - 20, w - 4):
+            q = x[200:200 + m]
+            r = x[200 - lead * shift:200 - lead * shift + m] + rng.normal(0.0, 0.2, m)
+            zq, zr = O.znorm(q).astype(np.float32), O.znorm(r).astype(np.float32)
+            d = O.dtw(zr.astype(np.float64), zq.astype(np.float64), w)
+            for f in (1.2, 1.0005):
+                (s, _), val = emu(zr, zq, d * f, 3, None, CE, w)
+                counts[s] = counts.get(s, 0) + 1
+                _check(s, val, d, d * f, d * f, (m, w, shift, f))
+    # paths near an edge are handed over (the rule keeps a margin of about
+    # 2 kElCE rows and a block's extent); a path 20 cells inside finishes
+    assert counts.get("done", 0) > 0 and counts.get("ovf", 0) > 0, counts

@@ -238,6 +238,31 @@ def test_doubled_check_interval_changes_work_not_results():
         assert torch.equal(bd0, bd1) and torch.equal(bi0, bi1)
 
 
+def test_elastic_and_one_warp_first_levels_agree():
+    """Every signature of a mixed batch (unconstrained and banded items, short
+    and long queries) forced to the elastic first level (tile 1; queries it
+    cannot run fall back to the built-in rule) and to the one-warp K = 32
+    level: bit-identical results, equal to the built-in choice's."""
+    rng = np.random.default_rng(29)
+    R_np = np.asarray(synth.random_walk(80_000, 30), np.float32)
+    with api.Context(0) as ctx:
+        R = dev(R_np)
+        rid = ctx.register(R)
+        items = mixed_items(rng, [(rid, R_np)], 8, 64, 2000, 1500)
+        Qd = {id(t[0]): dev(t[0]) for t in items}
+        dev_items = [(Qd[id(t[0])],) + t[1:] for t in items]
+        bi0, bd0 = ctx.search_batch(dev_items, 5)
+        for tile in (1, 32):
+            for lg in range(13):
+                for tenth in range(11):
+                    for band in (0, 1):
+                        ctx.set_first_tile(lg, tenth, band, tile)
+            assert ctx.get_first_tile(10, 10, 0) == tile
+            bi1, bd1 = ctx.search_batch(dev_items, 5)
+            assert torch.equal(bd0, bd1) and torch.equal(bi0, bi1), tile
+        compare_with_plain(ctx, items, {rid: R})
+
+
 def test_batched_mix_sample_against_the_oracle():
     """64 items of the batched mix (1,024 queries x 8 references, drawn among the
     four shortest references) as one batch, against the FP64 oracle's k nearest
