@@ -90,7 +90,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, 2) batch_elastic_kernel(c
         C.check2 = 0;
         C.dbg = nullptr;
         const long long c0 = clock64();
-        process_tile<kElK, BAND, true, 0, false, 2, false, 0, true>(C, nullptr, false, i0, nl, count);
+        process_tile<kElK, BAND, true, 0, false, 2, false, 0, true, false>(C, nullptr, false, i0, nl, count);
         if (lane == 0) atomicAdd(L.D.cost + it.state, static_cast<unsigned long long>(clock64() - c0));
     }
     __syncthreads();

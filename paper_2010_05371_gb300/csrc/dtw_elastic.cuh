@@ -98,7 +98,7 @@ static_assert(kElFillRows >= 32 && kElFillRows % 32 == 0, "whole warps of rows")
 
 // zr: minus row r (1-based), -z_r, at zr[r - 1] (so that d = q + (-z) is one
 // add, packed or not), NaN at zr[-kElPadRows .. -1] and
-// zr[nr .. nr + kElPadRows + 2); zq: column c at zq[c - 1] (c <= nc).  All 32 lanes call it
+// zr[nr .. nr + kElPadRows + 2); zq: column c at zq[c - 1] (c <= nc; see QPAD).  All 32 lanes call it
 // with identical arguments.  Returns busy = lane-steps executed by the
 // active windows (started or not).
 //
@@ -125,7 +125,12 @@ static_assert(kElFillRows >= 32 && kElFillRows % 32 == 0, "whole warps of rows")
 // every alive cell's optimal path lies in the band, so its value is the banded
 // DP's (the same operations on the same inputs; dead out-of-band values lose
 // every min to the alive ones), and the result is the banded EAPrunedDTW's.
-template <int J, int COST, bool BANDED, typename FillF>
+//
+// QPAD: zq holds NaN from zq[nc] through zq[nc + kElPadCols - 1] and is
+// 16-byte aligned (the one-query kernel's shared copy), so the column loads
+// need no test; otherwise (the batch's query in global memory) columns past nc
+// are NaN by a test.
+template <int J, int COST, bool BANDED, bool QPAD, typename FillF>
 __device__ __forceinline__ DtwOut dtw_elastic(const float* __restrict__ zr, const float* __restrict__ zq, int nr,
                                               int nc, const BestSoFar bsf, float ub, int w, FillF fill) {
     constexpr int K = kElK;
@@ -152,7 +157,7 @@ __device__ __forceinline__ DtwOut dtw_elastic(const float* __restrict__ zr, cons
     auto load_q = [&](int j) {
         const int c0 = (B0 + 32 * j + lane) * K;
         float4 v;
-        if (c0 + K <= nc && (reinterpret_cast<uintptr_t>(zq + c0) & 15) == 0) {
+        if (QPAD || (c0 + K <= nc && (reinterpret_cast<uintptr_t>(zq + c0) & 15) == 0)) {
             v = *reinterpret_cast<const float4*>(zq + c0);
         } else {
             const float nan = f_nan();

@@ -40,7 +40,9 @@ constexpr int kElBandMinQuarters = EAPDTW_ELASTIC_BAND_MIN_QUARTERS;
 // (w >= max(nr, nc) - 1 is unconstrained); tile_hint: 4, 8, 16 or 32 fixes the
 // first level's K, kGroupTileHint makes it a group of warps, 0 chooses.
 // search_levels: the first level may be the elastic wavefront (unconstrained,
-// or a band of at least kElBandMinW and a quarter of the query) or, on
+// or, for queries of up to 1024 points, a band of at least kElBandMinW and a
+// quarter of the query: longer ones come with wider live regions that it
+// mostly hands over) or, on
 // request, a group of warps; neither implements upper-bound tightening, and
 // the pair kernel has neither.
 inline Plan plan_levels(int64_t nr, int64_t nc, int64_t w, int tile_hint, bool search_levels = true) {
@@ -67,7 +69,7 @@ inline Plan plan_levels(int64_t nr, int64_t nc, int64_t w, int tile_hint, bool s
         // A wide band: the elastic wavefront first, handing the candidates
         // whose live region nears the band's edges (or outgrows its windows)
         // to the banded levels below.
-        if (search_levels && nc > 32 * 4 && w >= kElBandMinW && 4 * w >= kElBandMinQuarters * nc) {
+        if (search_levels && nc > 32 * 4 && nc <= 32 * 32 && w >= kElBandMinW && 4 * w >= kElBandMinQuarters * nc) {
             p.K[0] = kElK;
             p.band[0] = 1;
             p.wide[0] = false;

@@ -298,9 +298,10 @@ __device__ __forceinline__ bool tile_lanes(const TileCtx& C, const float* s_r, b
 // TIGHT: upper-bound tightening for the survivors (needs C.cbw and the lower
 // bounds; compiled out otherwise).
 // EL: run the survivors through the narrow-block elastic wavefront
-// (dtw_elastic.cuh; unconstrained, K = kElK, C.zr and C.zq padded as it needs).
+// (dtw_elastic.cuh; K = kElK, C.zr padded as it needs; ELQPAD: C.zq padded
+// with NaN and 16-byte aligned too).
 template <int K, int BAND, bool LB, int JW, bool STAGE = true, int ECM = 1, bool TIGHT = false, int COST = 0,
-          bool EL = false, typename CountF>
+          bool EL = false, bool ELQPAD = true, typename CountF>
 __device__ __forceinline__ void process_tile(const TileCtx& C, float* s_r, bool list_mode, int64_t i0,
                                              int nlanes, CountF count) {
     const int lane = threadIdx.x & 31;
@@ -364,7 +365,7 @@ __device__ __forceinline__ void process_tile(const TileCtx& C, float* s_r, bool 
                 for (int i = r0 + lane; i < r1; i += 32) zr[i] = -znorm1(xw[i], a_s, cw_s, isd_s);
                 __syncwarp();
             };
-            o = dtw_elastic<kElJ, COST, (BAND != 0)>(C.zr, C.zq, m, m, C.bsf, ub, C.w, fill);
+            o = dtw_elastic<kElJ, COST, (BAND != 0), ELQPAD>(C.zr, C.zq, m, m, C.bsf, ub, C.w, fill);
             __syncwarp();   // every lane is done with the rows before the next survivor's
         } else {
             constexpr int kJ = JW > 0 ? JW : dtw_windows(K, BAND);

@@ -109,16 +109,21 @@ GROUP_CASES = [
     ("ecg", 2_800, 2500, 1500, 2, 23, 512),   # five warps
     ("ecg", 2_800, 2500, 1500, 2, 23, 0),     # the same through the one-warp levels and re-runs
     ("walk", 4_300, 4096, 4096, 1, 24, 512),  # eight warps, unconstrained
+    # the elastic wavefront on a wide band as the first level (w >= 64 and a
+    # quarter of m), handing candidates near the band's edges to the banded levels
+    ("walk", 30_000, 300, 200, 2, 30, 0),
+    ("ecg", 20_000, 500, 130, 1, 31, 0),
+    ("walk", 12_000, 900, 300, 3, 32, 0),
 ]
 
 
 @pytest.mark.parametrize("kind,n,m,w,k,seed,tile", GROUP_CASES)
-def test_group_levels_bit_exact(kind, n, m, w, k, seed, tile):
+def test_group_and_banded_elastic_levels_bit_exact(kind, n, m, w, k, seed, tile):
     """The group wavefront as the first level (its warp 0 runs the
     lower-bound cascade of each tile, the group the survivors) or as the
-    re-run level: results equal the FP32 emulation's, and under a fixed bound
-    so do the prune, abandon and completion counts, with and without lower
-    bounds."""
+    re-run level, and the banded elastic first level: results equal the FP32
+    emulation's, and under a fixed bound so do the prune, abandon and
+    completion counts, with and without lower bounds."""
     R, Q = inputs(kind, n, m, seed)
     ei, ed, _ = O.o7_search(Q, R, w, k)
     Rd, Qd = dev(R), dev(Q)
@@ -131,5 +136,7 @@ def test_group_levels_bit_exact(kind, n, m, w, k, seed, tile):
         gi2, gd2, gc = api.subseq_search(Qd, Rd, w, k, audit_ub=ub, no_lb=not use_lb, tile=tile,
                                          return_counters=True)
         assert {c: gc[c] for c in AUDIT_KEYS} == oc, (use_lb, gc, oc)
+        if tile == 0 and m > 128 and w >= 64 and 4 * w >= m and w < m - 1:
+            assert gc["first_tile"] == 4, gc   # the elastic wavefront ran first
         np.testing.assert_array_equal(gd2.cpu().numpy(), ad)
         np.testing.assert_array_equal(gi2.cpu().numpy(), ai)
