@@ -225,10 +225,11 @@ def _stratum(m, ratio):
 def batched_section(args, dev):
     """Batched search (one graph-captured launch sequence over all items)
     against the one-query-per-call path on the same items: a stratified sample
-    of the 1,024-query mix (the first query of each of 16 length x window-ratio
-    strata, each against the 8 references), and the full mix's time estimated
-    from it (each stratum's measured one-call time weighted by its share of the
-    1,024 queries, times the sample's batched/one-call ratio)."""
+    of the 1,024-query mix (the first random-walk and the first ECG-like query
+    of each of 16 length x window-ratio strata, each against the 8
+    references), and the full mix's time estimated from it: each sampled
+    query's one-call time and the time of its 8 items as a batch of their own,
+    weighted by its (stratum, kind)'s share of the 1,024 queries."""
     import math
     import torch
     from paper_2010_05371_gb300 import api, synth
@@ -240,9 +241,9 @@ def batched_section(args, dev):
     counts = {}
     first = {}
     for q, (m, w, ecg, k, ratio) in enumerate(mix):
-        st = _stratum(m, ratio)
-        counts[st] = counts.get(st, 0) + 1
-        first.setdefault(st, q)
+        key = (_stratum(m, ratio), bool(ecg))
+        counts[key] = counts.get(key, 0) + 1
+        first.setdefault(key, q)
     picked = sorted(first.values())[:args.batch_queries]
     if args.batch_strata:   # profiling aid: only these of the sampled strata
         picked = [picked[int(j)] for j in args.batch_strata.split(",")]
@@ -289,15 +290,27 @@ def batched_section(args, dev):
     tp = sum(plain_ns) / 1e9
     mism = sum(0 if torch.equal(pd, bd[i, :k]) else 1
                for i, ((Q, rid, w, k), (pi, pd)) in enumerate(zip(items, plain)))
-    # the full mix, estimated per stratum from the sampled query's one-call times
+    # each sampled query's items as a batch of their own (device time; the
+    # launch sequence is captured and its kernels loaded by the runs above)
     per_query_ns = {}
     for q, ns in zip(item_query, plain_ns):
         per_query_ns[q] = per_query_ns.get(q, 0) + ns
-    est_plain_s = sum(counts[_stratum(mix[q][0], mix[q][4])] * per_query_ns[q] for q in picked) / 1e9
+    per_query_batch_ns = {}
+    for q in picked:
+        own = [it for it, iq in zip(items, item_query) if iq == q]
+        _, _, c1 = ctx.search_batch(own, 5, return_counters=True)
+        per_query_batch_ns[q] = c1["ns_total"]
+    torch.cuda.synchronize()
+    # the full mix: each (stratum, kind)'s share of the 1,024 queries x its sampled query's times
+    weight = {q: counts[(_stratum(mix[q][0], mix[q][4]), bool(mix[q][2]))] for q in picked}
+    est_plain_s = sum(weight[q] * per_query_ns[q] for q in picked) / 1e9
+    est_batch_s = sum(weight[q] * per_query_batch_ns[q] for q in picked) / 1e9
+    wins = sum(1 for q in picked if per_query_batch_ns[q] < per_query_ns[q])
     full_windows = sum(sum(n - m + 1 for n in lens) for (m, w, ecg, k, ratio) in mix)
     ctx.close()
     return {
-        "config": (f"batched mix: {len(picked)} queries, the first of each length x window-ratio stratum of the "
+        "config": (f"batched mix: {len(picked)} queries, the first random-walk and the first ECG-like query of each "
+                   f"length x window-ratio stratum of the "
                    f"{BATCH_FULL_QUERIES}-query mix (m log-uniform 64-2048, window ratio uniform 0-1, random walk "
                    f"or ECG-like, k in {{1,5}}, seed {BATCH_QUERY_SEED}) x 8 random-walk references (n log-uniform "
                    f"1e5-1e7, seed {BATCH_REF_SEED}), every query against every reference"),
@@ -314,10 +327,14 @@ def batched_section(args, dev):
         "batched_queries_per_s": len(items) / tb, "plain_queries_per_s": len(items) / tp,
         "speedup": tp / tb, "executed_cells_per_s": cnt["cells"] / tb,
         "identical_to_plain": f"{len(items) - mism}/{len(items)} items bit-identical distances",
+        "per_query": {"queries": len(picked), "batch_faster": wins,
+                      "speedup_median": statistics.median(per_query_ns[q] / per_query_batch_ns[q] for q in picked)},
         "full_mix_estimate": {
             "queries": BATCH_FULL_QUERIES, "items": BATCH_FULL_QUERIES * len(refs), "windows": full_windows,
-            "plain_s": round(est_plain_s, 2), "batched_s": round(est_plain_s * tb / tp, 2),
-            "basis": "stratum counts of the full mix x each stratum's sampled one-call time; batched = that x the sample's batched/one-call ratio"},
+            "plain_s": round(est_plain_s, 2), "batched_s": round(est_batch_s, 2),
+            "speedup": est_plain_s / est_batch_s,
+            "basis": ("(stratum, kind) counts of the full mix x that (stratum, kind)'s sampled query: its one-call "
+                      "times, and its items as a batch of their own (device time)")},
     }
 
 
@@ -498,8 +515,9 @@ def main():
                     help="searches per step (profiling aid; the benchmark is 'all')")
     ap.add_argument("--queries", default="1,2,3,4",
                     help="query seeds of the step (profiling aid; the benchmark is all four)")
-    ap.add_argument("--batch-queries", type=int, default=16,
-                    help="strata sampled from the batched mix (one query each, against 8 references); 0 skips it")
+    ap.add_argument("--batch-queries", type=int, default=32,
+                    help="queries sampled from the batched mix (the first of each stratum and kind, against 8 "
+                         "references); 0 skips it")
     ap.add_argument("--batch-strata", default="",
                     help="indices into the sampled strata to run alone (profiling aid; the benchmark runs all)")
     ap.add_argument("--serve-requests", type=int, default=24,

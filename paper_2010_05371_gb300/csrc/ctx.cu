@@ -903,6 +903,8 @@ int32_t eapdtw_search_batch(eapdtw_ctx* c, const eapdtw_item* items, int32_t n, 
     return rc;
 }
 
+constexpr float kTuneMargin = 0.03f;   // a tuned choice must beat the built-in one by 3% on the sample
+
 int32_t eapdtw_autotune(eapdtw_ctx* c, const eapdtw_item* items, int32_t n, int64_t sample_windows, void* stream,
                         int32_t* n_tuned) {
     if (!c || !items || n < 1 || sample_windows < 1) return EAPDTW_ERR_INVALID_ARG;
@@ -958,7 +960,10 @@ int32_t eapdtw_autotune(eapdtw_ctx* c, const eapdtw_item* items, int32_t n, int6
             cand[1] = base * 2;
             cand[2] = base / 2;
         }
-        float best_ms = INFINITY;
+        // the built-in choice (the first candidate at the built-in interval)
+        // stays unless another one is faster by kTuneMargin on the sample: a
+        // sample's small differences did not carry over to whole references
+        float best_ms = INFINITY, builtin_ms = INFINITY;
         std::pair<int, int> best(cand[0], 0);
         for (int chk = 0; chk < 2 && rc == EAPDTW_OK; ++chk) {
             for (int K : cand) {
@@ -969,12 +974,14 @@ int32_t eapdtw_autotune(eapdtw_ctx* c, const eapdtw_item* items, int32_t n, int6
                 if (rc == EAPDTW_OK) rc = run_batch(c, &it, 1, it.k, d_idx, d_dist, nullptr, stream, &len, &ms2);
                 if (rc != EAPDTW_OK) break;
                 ms = std::min(ms, ms2);
+                if (K == cand[0] && chk == 0) builtin_ms = ms;
                 if (ms < best_ms) {
                     best_ms = ms;
                     best = std::make_pair(K, chk);
                 }
             }
         }
+        if (!(best_ms < builtin_ms * (1.0f - kTuneMargin))) best = std::make_pair(cand[0], 0);
         if (rc != EAPDTW_OK) {
             c->tuned.erase(kv.first);
             break;
