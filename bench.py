@@ -52,9 +52,9 @@ GOLDEN = os.path.join(ROOT, "tests", "golden", "bench_large_oracle.json")
 PEAK_STEPS = 1 << 18
 PEAK_MODES = (0, 1, 2, 3)
 # DRAM bytes (read + write) of the dominant search kernel per search: the ncu
-# capture of the elastic first-level launch at n = 1e7 (208.3 MB for 9,998,977
+# capture of the elastic first-level launch at n = 1e7 (207.8 MB for 9,998,977
 # windows), scaled to the workload's 19,998,977 windows.
-TRAFFIC_BYTES_PER_SEARCH = 4.166e8
+TRAFFIC_BYTES_PER_SEARCH = 4.156e8
 # CPU baseline sample (oracle): windows of the cascade (w=103) and nolb (w=1024) searches
 CPU_SAMPLE = {"cascade_windows": 2_000_000, "nolb_windows": 200_000, "query_seed": 1}
 
@@ -264,7 +264,7 @@ def batched_section(args, dev):
     torch.cuda.synchronize()
     fixed_s = cnt_fixed["ns_total"] / 1e9
     t0 = time.perf_counter()
-    tuned = ctx.autotune(items, sample_windows=1 << 18)   # first-level tile and check interval per signature
+    tuned = ctx.autotune(items, sample_windows=1 << 20)   # first-level tile and check interval per signature
     tune_s = time.perf_counter() - t0
     tuning = ctx.tuning_table()
     dev_ms, host_s = [], []

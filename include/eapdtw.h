@@ -341,7 +341,7 @@ int32_t eapdtw_get_tuning(eapdtw_ctx* ctx, int32_t log2_m, int32_t ratio_tenths,
  * K and twice that), each at
  * the built-in check interval and at twice it (two runs each, the faster
  * counts, device time of the launch sequence), and enters the fastest pair if
- * it beats the built-in choice by 3% (else the built-in choice).
+ * it beats the built-in choice by 5% (else the built-in choice).
  * *n_tuned (optional) receives the number of signatures entered.  Blocking;
  * results of later searches are unchanged. */
 int32_t eapdtw_autotune(eapdtw_ctx* ctx, const eapdtw_item* items, int32_t n, int64_t sample_windows,

@@ -903,7 +903,7 @@ int32_t eapdtw_search_batch(eapdtw_ctx* c, const eapdtw_item* items, int32_t n, 
     return rc;
 }
 
-constexpr float kTuneMargin = 0.03f;   // a tuned choice must beat the built-in one by 3% on the sample
+constexpr float kTuneMargin = 0.05f;   // a tuned choice must beat the built-in one by 5% on the sample
 
 int32_t eapdtw_autotune(eapdtw_ctx* c, const eapdtw_item* items, int32_t n, int64_t sample_windows, void* stream,
                         int32_t* n_tuned) {
