@@ -25,7 +25,14 @@
 namespace eapdtw {
 
 constexpr int kWarpsPerBlock = 8;
-constexpr int kLbUnroll = 8;
+// LB_Keogh terms per early-exit test (a compile-time knob for tuning
+// experiments; the query arrays are padded to a multiple of it with neutral
+// terms).  A window is pruned iff its whole sum exceeds the bound, whatever
+// the spacing of the tests, so the spacing changes work, not results.
+#ifndef EAPDTW_LB_UNROLL
+#define EAPDTW_LB_UNROLL 8
+#endif
+constexpr int kLbUnroll = EAPDTW_LB_UNROLL;
 
 struct SearchArgs {
     RefView ref;
