@@ -42,12 +42,9 @@ constexpr int kBatchSlots = 64;      // k-best slots per item (k <= 64)
 // Bits of an item's flags.
 constexpr int kFlagLost = 1;         // an overflow entry did not fit a re-run list
 constexpr int kFlagTimeout = 2;      // a device-side wait of the group level ran out
-// Query copies of the widest levels (JW windows of 32 blocks of 32 columns).
-__host__ __device__ constexpr int wide_cols(int JW) { return JW * 1024; }
-__host__ __device__ constexpr size_t wide_smem(int JW) { return sizeof(float) * kWarpsPerBlock * wide_cols(JW); }
-
+// Block width a level's band mode is chosen for: the one-warp levels' K, and
+// 32 for the group levels (a band mode valid at K = 32 is valid at their 16).
 __host__ __device__ constexpr int batch_level_K(int level) { return level < 4 ? (4 << level) : 32; }
-__host__ __device__ constexpr int batch_level_windows(int level) { return level == 4 ? 2 : (level == 5 ? 4 : 0); }
 // The widest level a query of m points needs (3 for m <= 1024).
 __host__ __device__ constexpr int batch_last_level(int m) { return m <= 1024 ? 3 : (m <= 2048 ? 4 : 5); }
 
@@ -133,24 +130,20 @@ struct BatchLaunch {
     float lb_scale;
 };
 
-// Persistent batch kernel: the cascade and wavefront of process_tile, the
-// windows read from global memory (items differ in length).  The query is
-// read from global memory too, except at the widest level (JW > 1 windows),
-// which streams the column values at every step: there each warp first copies
-// the item's query into its slot of dynamic shared memory (wide_cols(JW) floats).
-// A seed launch (scls >= 0) runs the seed windows of its class, before any
-// tile: their exact distances tighten each item's bound, as the one-query
-// search's seed pass does.  It runs at the widest level, where no live region
-// overflows.
-template <int K, int BAND, int JW>
-__global__ void __launch_bounds__(kWarpsPerBlock * 32, mode_min_blocks(K, BAND, JW))
+// Persistent batch kernel of the one-warp levels: the cascade and wavefront
+// of process_tile, the windows and the query read from global memory through
+// L1 (items differ in length).  A seed launch (scls >= 0) runs the seed
+// windows of its class, before any tile: their exact distances tighten each
+// item's bound, as the one-query search's seed pass does.  It runs at the
+// item's widest level, where no live region overflows (K = 32 here for
+// queries of up to 1024 points; the group levels run the longer ones).
+template <int K, int BAND>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32, mode_min_blocks(K, BAND, 0))
 batch_kernel(const BatchLaunch L) {
     __shared__ unsigned long long s_cnt[kNumCounters];
-    extern __shared__ __align__(16) float s_q[];
     if (threadIdx.x < kNumCounters) s_cnt[threadIdx.x] = 0;
     __syncthreads();
     const int lane = threadIdx.x & 31;
-    const int warp = threadIdx.x >> 5;
     int cn = 0, c0 = 0, sn = 0, s0 = 0;
     int64_t ntiles = 0;
     const int64_t* P = nullptr;
@@ -216,13 +209,6 @@ batch_kernel(const BatchLaunch L) {
         TileCtx C;
         C.ref = it.ref;
         C.zq = it.zq;
-        if (JW > 1 && it.m <= wide_cols(JW)) {
-            float* q = s_q + warp * wide_cols(JW);
-            __syncwarp();
-            for (int j = lane; j < it.m; j += 32) q[j] = it.zq[j];
-            __syncwarp();
-            C.zq = q;
-        }
         C.uq = it.uq;
         C.lq = it.lq;
         C.zqo = it.zqo;
@@ -254,7 +240,7 @@ batch_kernel(const BatchLaunch L) {
         C.lost = seed ? nullptr : L.D.flags + it.state;   // a seed is only a hint: nothing is lost
         C.dbg = nullptr;
         const long long c0 = clock64();
-        process_tile<K, BAND, JW <= 1, JW, false, 2>(C, nullptr, list, i0, nl, count);
+        process_tile<K, BAND, true, 0, false, 2>(C, nullptr, list, i0, nl, count);
         if (lane == 0) atomicAdd(L.D.cost + it.state, static_cast<unsigned long long>(clock64() - c0));
     }
     __syncthreads();

@@ -18,13 +18,13 @@ constexpr int K = EAPDTW_UNIT_K;
 
 template <int BAND>
 cudaError_t launch_band(const BatchLaunch& args, int blocks, cudaStream_t s) {
-    batch_kernel<K, BAND, 0><<<blocks, kWarpsPerBlock * 32, 0, s>>>(args);
+    batch_kernel<K, BAND><<<blocks, kWarpsPerBlock * 32, 0, s>>>(args);
     return cudaGetLastError();
 }
 template <int BAND>
 int occupancy_blocks() {
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel<K, BAND, 0>, kWarpsPerBlock * 32, 0) !=
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel<K, BAND>, kWarpsPerBlock * 32, 0) !=
         cudaSuccess) {
         cudaGetLastError();
         per_sm = 1;
@@ -37,7 +37,7 @@ int occupancy_blocks() {
 template <int BAND>
 cudaError_t attributes() {
     // the windows and the query are read through L1: give it the whole carveout
-    return cudaFuncSetAttribute(batch_kernel<K, BAND, 0>, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
+    return cudaFuncSetAttribute(batch_kernel<K, BAND>, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
 }
 }  // namespace
 

@@ -424,9 +424,10 @@ __host__ __device__ constexpr int mode_min_blocks(int K, int BAND, int JW) {
 
 // LB: compile the lower-bound cascade in (true) or out (false, the "nolb"
 // variant and the list-mode re-runs); leaving it out frees registers.
-// JW: 0 for the column values in registers; JW >= 1 streams them from the
-// query in shared memory with JW windows of 32 blocks (the widest re-run level
-// uses four: 4096 columns at K = 32, one resident block per SM).
+// JW: 0 for the column values in registers (every level built by default);
+// JW >= 1 streams them from the query in shared memory with JW windows of 32
+// blocks (kept for tuning experiments through EAPDTW_KJW; the widest re-run
+// level is the group wavefront, search_wide.cu).
 // COST: see dtw_warp (the absolute cost is built for the no-lower-bound search only).
 template <int K, int BAND, bool LB, int JW = 0, bool TIGHT = false, int COST = 0>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32, mode_min_blocks(K, BAND, JW))
