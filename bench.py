@@ -496,8 +496,11 @@ def run_reference(args):
     cb["value"] = v
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "windows/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(secs),
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": workload_desc(args.n), "sample": cb["sample"]},
+            "higher_is_better": True, "scaling": "strong", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": workload_desc(args.n), "n": args.n, "m": M, "queries": len(QUERY_SEEDS),
+                       "w": [w for w, _ in SEARCHES], "k": 1, "parallelism": "host cores of rank 0",
+                       "sample": cb["sample"]},
             "cpu_baseline": cb,
             "e2e": {"value": v, "unit": "windows/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
