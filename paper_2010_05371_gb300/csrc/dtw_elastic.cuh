@@ -83,7 +83,11 @@ constexpr int kElPadCols = 32 * kElJ * kElK;
 
 // Floats of the per-warp row buffer (rows start at offset kElPadRows) and of
 // the query buffer (NaN past the last column) for queries of m points.
-__host__ __device__ constexpr int elastic_row_floats(int m) { return (2 * kElPadRows + m + kElR + 3) / 4 * 4; }
+// (after the NaN rows past the last row, 8 floats hold the survivor's
+// z-normalisation coefficients and window pointer for the on-demand fill)
+__host__ __device__ constexpr int elastic_row_floats(int m) { return (2 * kElPadRows + m + 12 + 3) / 4 * 4; }
+// Offset, from row 1, of those 8 floats.
+__host__ __device__ constexpr int elastic_fill_slot(int m) { return m + kElPadRows + 4; }
 __host__ __device__ constexpr int elastic_col_floats(int m) { return (m + kElPadCols + 3) / 4 * 4; }
 // Cells one busy lane-step computes.
 constexpr int kElCellsPerStep = kElK * kElR;
