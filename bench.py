@@ -51,10 +51,12 @@ GOLDEN = os.path.join(ROOT, "tests", "golden", "bench_large_oracle.json")
 # fastest mode is the roofline's peak.
 PEAK_STEPS = 1 << 18
 PEAK_MODES = (0, 1, 2, 3)
-# DRAM bytes (read + write) of the dominant search kernel per search: the ncu
-# capture of the elastic first-level launch at n = 1e7 (207.8 MB for 9,998,977
-# windows), scaled to the workload's 19,998,977 windows.
-TRAFFIC_BYTES_PER_SEARCH = 4.156e8
+# DRAM bytes (read + write) of the dominant search kernel per search, from an
+# ncu capture of the kernel as built (scaled from n = 1e7 to the workload's
+# 19,998,977 windows), or None when the kernel has changed since the last
+# capture.  The last one (207.8 MB for 9,998,977 windows, 20.8 B per window)
+# predates keeping the row fill's inputs in shared memory.
+TRAFFIC_BYTES_PER_SEARCH = None
 # CPU baseline sample (oracle): windows of the cascade (w=103) and nolb (w=1024) searches
 CPU_SAMPLE = {"cascade_windows": 2_000_000, "nolb_windows": 200_000, "query_seed": 1}
 
