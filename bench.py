@@ -224,6 +224,19 @@ def _stratum(m, ratio):
     return lb * 4 + min(3, int(ratio * 4))
 
 
+def sample_strata(mix, nq):
+    """The batched sample: the first random-walk and the first ECG-like query
+    of each (length x window-ratio stratum), in draw order, at most nq of them;
+    and each (stratum, kind)'s count in the whole mix (the weights of the
+    full-mix estimate)."""
+    counts, first = {}, {}
+    for q, (m, w, ecg, k, ratio) in enumerate(mix):
+        key = (_stratum(m, ratio), bool(ecg))
+        counts[key] = counts.get(key, 0) + 1
+        first.setdefault(key, q)
+    return sorted(first.values())[:nq], counts
+
+
 def batched_section(args, dev):
     """Batched search (one graph-captured launch sequence over all items)
     against the one-query-per-call path on the same items: a stratified sample
@@ -240,13 +253,7 @@ def batched_section(args, dev):
     refs = [torch.from_numpy(synth.random_walk(n, 100 + j).astype(np.float32)).to(dev)
             for j, n in enumerate(lens)]
     mix = batched_mix(BATCH_FULL_QUERIES)
-    counts = {}
-    first = {}
-    for q, (m, w, ecg, k, ratio) in enumerate(mix):
-        key = (_stratum(m, ratio), bool(ecg))
-        counts[key] = counts.get(key, 0) + 1
-        first.setdefault(key, q)
-    picked = sorted(first.values())[:args.batch_queries]
+    picked, counts = sample_strata(mix, args.batch_queries)
     if args.batch_strata:   # profiling aid: only these of the sampled strata
         picked = [picked[int(j)] for j in args.batch_strata.split(",")]
     queries = []
