@@ -214,3 +214,26 @@ def test_equal_series_finish_at_zero():
     x = O.znorm(synth.random_walk(1100, 5)).astype(np.float32)
     val, _ = run_group(x, x, 1100, 0.5, rng)
     assert val == 0.0, val
+
+
+def test_eight_warp_group():
+    """The largest group (4096 columns, eight warps, the batch's level 5 and
+    the one-query search's queries of up to 4096 points): short windows
+    against a 4096-point query, unconstrained and banded, bounds from +inf to
+    below the DTW; every interleaving the waits allow, in random order."""
+    rng = np.random.default_rng(17)
+    R = synth.random_walk(10_000, 71)
+    zq = O.znorm(synth.random_walk(4096, 72)).astype(np.float32)
+    outcomes = {}
+    for nr in (40, 90):
+        i = int(rng.integers(0, len(R) - nr))
+        zr = O.znorm(R[i:i + nr]).astype(np.float32)
+        for w in (4096, 4096 - nr + 30):
+            d = O.dtw(zr.astype(np.float64), zq.astype(np.float64), w)
+            for f in (np.inf, 1.0005, 0.7):
+                ub = d * f if np.isfinite(f) else np.inf
+                val, _ = run_group(zr, zq, w, ub, rng)
+                key = "done" if val <= ub else "inf"
+                outcomes[key] = outcomes.get(key, 0) + 1
+                _check(val, d, ub, (nr, w, f))
+    assert outcomes.get("done", 0) > 0 and outcomes.get("inf", 0) > 0, outcomes
